@@ -1,0 +1,289 @@
+"""Benchmark: element matrices per second of batched element-local assembly.
+
+Workload (one step = one pass of the whole hot path over one batch): the
+Helmholtz form  int grad u . grad v + f u v  with P2 test/trial functions and
+a P2 coefficient f, on 1,000,000 random affine tetrahedra (collapsed
+Gauss-Jacobi 4^3 = 64-point rule, 10 x 10 FP64 element matrices), inputs
+resident in HBM.  Each step is one launch of the flop-reduced kernel chosen by
+the planner (pre-evaluated reference tensors, FP32 contraction, FP64
+geometry).
+
+Also reported: the plain FP64 GPU kernel (the comparator) on the same
+workload, the end-to-end rate through the host-buffer C ABI call (copies
+inside the timed region), the roofline of the dominant kernel against the
+measured HBM bandwidth, clocks during the timed region, and the FP64 CPU
+oracle on a bounded sample of the workload (rank 0, N = 1).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "helmholtz_p2_1M", "form": "helmholtz", "degree": 2, "elements": 1_000_000,
+            "quad_points": 64, "local_matrix": "10x10 f64"}
+METRIC = "element matrices/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1604_05872_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", "helmholtz_p2_pre_1M.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7 and parts[0].isdigit():
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [int(r[0]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": int(rows[0][1]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def make_inputs(E, seed_offset=0):
+    from paper_1604_05872_gb300 import inputs
+    coords, f = inputs.workload(inputs.HELMHOLTZ, 2, E, seed=inputs.SEED + seed_offset)
+    return coords, f
+
+
+def cpu_baseline(coords, f, budget_s=15.0):
+    """FP64 oracle on a bounded sample of the workload (host cores, OpenMP over elements)."""
+    import oracle
+    threads = max(1, os.cpu_count() or 1)
+    n = 2000
+    t0 = time.perf_counter()
+    oracle.assemble(1, 2, coords[:n], f[:n], nthreads=threads)
+    dt = time.perf_counter() - t0
+    n2 = int(min(len(coords), max(n, n * budget_s / max(dt, 1e-3) * 0.8)))
+    t0 = time.perf_counter()
+    oracle.assemble(1, 2, coords[:n2], f[:n2], nthreads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n2 / dt, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": "first %d of the 1M Helmholtz P2 elements, FP64 quadrature-mode loop nest, %.1f s" % (n2, dt)}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle as it stands, on host cores."""
+    if rank != 0:
+        return
+    coords, f = make_inputs(20000)
+    import oracle
+    threads = max(1, os.cpu_count() or 1)
+    per = 2000
+    for _ in range(args.warmup):
+        oracle.assemble(1, 2, coords[:per], f[:per], nthreads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s = (k * per) % (len(coords) - per)
+        oracle.assemble(1, 2, coords[s:s + per], f[s:s + per], nthreads=threads)
+    dt = time.perf_counter() - t0
+    value = args.steps * per / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, sample_per_step=per),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
+                             "sample": "%d elements of the workload per step" % per},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--elements", type=int, default=WORKLOAD["elements"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1604_05872_gb300 as fea
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fea.load()
+    E = args.elements
+    coords, f = make_inputs(E, seed_offset=rank)  # each rank its own shard (weak scaling)
+    from paper_1604_05872_gb300 import inputs
+    c = torch.from_numpy(coords).cuda()
+    fc = torch.from_numpy(inputs.coeff_array(1, 2, f)).cuda()
+    out = fea.empty_out(1, 2, E)
+    stream = torch.cuda.current_stream()
+    pl = fea.plan(1, 2)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        fea.assemble(1, 2, c, fc, out=out)
+    fea.sync()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fea.assemble(1, 2, c, fc, out=out)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    fea.sync()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = E * world / (ms_max * 1e-3)
+
+    # plain FP64 comparator on the same workload
+    for _ in range(1):
+        fea.assemble(1, 2, c, fc, out=out, precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
+    barrier()
+    nsteps = 2
+    ev0.record(stream)
+    for _ in range(nsteps):
+        fea.assemble(1, 2, c, fc, out=out, precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
+    ev1.record(stream)
+    barrier()
+    ms_naive = ev0.elapsed_time(ev1) / nsteps
+    fea.sync()
+
+    # end to end through the host-buffer C ABI call (copies inside the timed region)
+    hc = torch.from_numpy(coords).pin_memory()
+    hf = fc.cpu().pin_memory()
+    ho = torch.empty((E, 10, 10), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        fea.assemble_host(1, 2, hc, hf, ho)
+    barrier()
+    e2e_steps = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fea.assemble_host(1, 2, hc, hf, ho)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+
+    hbm, peak_kind = peaks()
+    alg_bytes = E * pl["bytes"]
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, variant=fea.VARIANT_NAMES[pl["variant"]], tile=pl["tile"],
+                       geometry="f64", contraction="f32", parallelism="dp%d (element shards)" % world,
+                       l2="inputs+outputs %.0f MB per step > 129 MB L2; no flush" % (alg_bytes / 1e6)),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes},
+        "comparator": {"kernel": "plain FP64 quadrature nest", "value": E / (ms_naive * 1e-3), "unit": METRIC,
+                       "ms_per_step": ms_naive, "speedup": ms_naive / ms},
+        "e2e": {"value": E * world / (e2e_ms * 1e-3), "unit": METRIC, "h2d_bytes_per_step": E * (96 + 80),
+                "d2h_bytes_per_step": E * 800, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "gflops": E * pl["flops_run"] / (ms * 1e-3) / 1e9,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(coords, f)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

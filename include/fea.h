@@ -1,0 +1,162 @@
+/*
+ * fea.h -- C ABI of the GB300 (sm_103a) batched element-local assembly library.
+ *
+ * For every tetrahedron e of a batch the library computes the local element
+ * matrix  A_e[i][j] = sum_q w_q |det J_e| F(phi_i, phi_j, coefficients, J_e^-1)(X_q)
+ * (Section 2.2, equation "quadrature"; the statement of local assembly is in
+ * Section 2), in the flop-reduced forms that the paper's transformation
+ * algorithm selects between: sharing elimination (Section 3.2, Algorithm 1)
+ * and pre-evaluation of the quadrature reduction (Section 3.3, Algorithm 2),
+ * coordinated by the cost function theta and Algorithm 3 (Section 4).
+ *
+ * Forms (Section 7 names them Mass, Helmholtz, Elasticity, Hyperelasticity):
+ *   FEA_MASS        int u v
+ *   FEA_HELMHOLTZ   int grad u . grad v + f u v,        f in P_p
+ *   FEA_ELASTICITY  int 2 mu eps(u):eps(v) + lam div u div v,  mu, lam in P_1
+ *   FEA_NEOHOOKEAN  tangent stiffness of W = mu/2 (tr C - 3) - mu ln J + lam/2 (ln J)^2
+ * Degrees p = 1..4 (Lagrange, equispaced nodes) on tetrahedra.
+ *
+ * Data layout (all arrays are C-contiguous, little-endian IEEE):
+ *   coords  double [E][4][3]  vertex coordinates; J[r][c] = x_{c+1}[r] - x_0[r].
+ *   coeffs  double, per element (fea_coeff_len doubles each):
+ *             mass: none (may be NULL);  helmholtz: f DOFs [n_p];
+ *             elasticity: mu DOFs [4] then lambda DOFs [4] (P_1 vertex values);
+ *             neohookean: displacement DOFs [n_p][3] (component fastest), and
+ *             after the last element two doubles: the constants mu, lambda.
+ *           fea_coeffs_size() gives the total length.
+ *   out     [E][n][n] row-major, n = fea_local_dim(); test index = row, trial
+ *           index = column; vector forms use DOF index 3*a + c.  double by
+ *           default, float when fea_options.out_f32 = 1.
+ *   DOF order of P_p: vertices 0..3; edges (2,3),(1,3),(1,2),(0,3),(0,2),(0,1)
+ *           with nodes running from the lower to the higher vertex; faces
+ *           opposite vertices 0..3; interior.  Inside a face or the interior,
+ *           nodes are ordered by barycentric index with the entity's last
+ *           vertex varying slowest.
+ *
+ * Ownership: the caller owns coords, coeffs and out.  In fea_assemble /
+ * fea_assemble_ex / fea_assemble_batch they are DEVICE pointers of the current
+ * CUDA device (16-byte aligned); host pointers are rejected with FEA_EINVAL --
+ * there is no CPU fallback.  fea_assemble_host takes HOST pointers and does the
+ * copies itself.  The library owns only its plan cache, its device-resident
+ * basis/reference tables and a reusable staging workspace; fea_finalize frees
+ * them.
+ *
+ * Errors: every call returns an fea_status and never aborts.  Device calls are
+ * asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ * default stream).  A degenerate element (det J == 0, or det F <= 0 for the
+ * Neo-Hookean form) writes NaN into that element's matrix and sets a device
+ * error word; fea_sync() returns FEA_EDEGENERATE once for it.
+ * fea_last_error() returns a message for the last failing call of this thread.
+ */
+#ifndef FEA_H
+#define FEA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { FEA_MASS = 0, FEA_HELMHOLTZ = 1, FEA_ELASTICITY = 2, FEA_NEOHOOKEAN = 3 } fea_form;
+
+typedef enum {
+  FEA_OK = 0,
+  FEA_EINVAL = 1,       /* bad argument (form, degree, size, pointer kind, alignment, option) */
+  FEA_ENOMEM = 2,       /* table or workspace allocation failed */
+  FEA_ECUDA = 3,        /* a CUDA runtime call failed (message in fea_last_error) */
+  FEA_EDEGENERATE = 4,  /* a degenerate element was met (NaN written for it) */
+  FEA_ETIMEOUT = 5      /* a bounded wait in the batch work queue gave up */
+} fea_status;
+
+/* Arithmetic of the contraction.  Geometry (J, det J and the adjugate of J,
+ * i.e. det J * J^-1) and the Neo-Hookean det F, F^-1, ln det F are FP64 in
+ * every mode. */
+typedef enum {
+  FEA_PREC_FP64 = 0,  /* everything FP64 (parity path, <= 1e-12 relative) */
+  FEA_PREC_FP32 = 1   /* FP32 contraction and pointwise work, FP64 geometry */
+} fea_precision;
+
+/* Loop-nest variant (Section 4, Figure "loopnest-opt"). */
+typedef enum {
+  FEA_VARIANT_AUTO = -1, /* Algorithm 3 choice, refined by the tuner when enabled */
+  FEA_VARIANT_NAIVE = 0, /* plain quadrature nest in normal form, FP64 (the comparator) */
+  FEA_VARIANT_SE = 1,    /* quadrature nest after sharing elimination (Algorithm 1) */
+  FEA_VARIANT_PRE = 2    /* pre-evaluated reference tensors (Algorithm 2) */
+} fea_variant;
+
+typedef struct {
+  int precision;       /* fea_precision (default FEA_PREC_FP32) */
+  int out_f32;         /* 0: out is double, 1: out is float */
+  int variant;         /* fea_variant (default FEA_VARIANT_AUTO) */
+  int tile;            /* elements per CTA tile, 0 = planner default */
+  size_t smem_budget;  /* T_H of Constraint 2 in bytes of shared memory, 0 = device limit */
+} fea_options;
+
+/* One request of a batch (fea_assemble_batch): device pointers as above. */
+typedef struct {
+  int form;
+  int degree;
+  int64_t E;
+  const double* coords;
+  const double* coeffs;
+  void* out;
+} fea_request;
+
+/* Plan summary (fea_plan). */
+typedef struct {
+  int variant;          /* variant that will run */
+  int tile;             /* elements per CTA tile */
+  int threads;          /* threads per CTA */
+  int quad_points;      /* Q of the rule */
+  int ref_terms;        /* r: reference tensors (pre-evaluation) */
+  size_t smem_bytes;    /* dynamic shared memory per CTA */
+  int64_t flops_naive;  /* per element, plain quadrature nest (normal form) */
+  int64_t flops_se;     /* per element, after sharing elimination */
+  int64_t flops_pre;    /* per element, after pre-evaluation (-1: not applicable) */
+  int64_t flops_run;    /* per element, variant that will run */
+  int64_t bytes;        /* per element, algorithmic HBM bytes (inputs + output) */
+} fea_plan_info;
+
+/* Sizes.  Return -1 for an unsupported (form, degree). */
+int fea_local_dim(int form, int degree);                /* n: n_p or 3 n_p */
+int fea_coeff_len(int form, int degree);                /* doubles per element */
+int64_t fea_coeffs_size(int form, int degree, int64_t E); /* total doubles in coeffs */
+int fea_quad_points(int form, int degree);              /* Q of the rule used */
+
+/* Assemble E element matrices on `stream` (device pointers).  fea_assemble
+ * uses default options (FP32 contraction, double output, variant AUTO). */
+int fea_assemble(int form, int degree, int64_t E, const double* coords,
+                 const double* coeffs, void* out, void* stream);
+int fea_assemble_ex(int form, int degree, int64_t E, const double* coords,
+                    const double* coeffs, void* out, const fea_options* opt, void* stream);
+
+/* Same, with HOST buffers: copies coords/coeffs to the device, assembles and
+ * copies the result back, then synchronises `stream`.  Pinned host memory
+ * gives the full copy bandwidth; work is pipelined over chunks. */
+int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host,
+                      const double* coeffs_host, void* out_host, const fea_options* opt,
+                      void* stream);
+
+/* Uneven batch of requests in one persistent launch (captured once into a CUDA
+ * graph per distinct batch shape and replayed).  Tiles are pulled from a work
+ * list with an atomic counter; all requests use the same options. */
+int fea_assemble_batch(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
+
+/* Wait for `stream`, then report (and clear) the device error word. */
+int fea_sync(void* stream);
+
+/* Plan for (form, degree, options) without launching anything. */
+int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info);
+
+/* Operation counts per element (Definition 8 counting: adds and products, an
+ * FMA counts 2) of the plain nest and of `variant` (AUTO = Algorithm 3 pick). */
+int fea_op_count(int form, int degree, int variant, int64_t* naive_flops, int64_t* opt_flops);
+
+const char* fea_last_error(void);
+void fea_finalize(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEA_H */

@@ -1,1 +1,187 @@
-"""GB300-native batched element-local assembly (see include/fea.h)."""
+"""GB300 (sm_103a) batched element-local assembly.
+
+Thin Python binding of the C ABI declared in include/fea.h: argument
+marshalling only.  Every step of the assembly runs in the CUDA library
+libfea.so (built in-tree by ``build.py``); there is no CPU fallback, and every
+call raises ``FeaError`` if the library is missing or a call fails.
+
+Tensors are torch tensors (device memory and streams come from PyTorch):
+coords float64 [E, 4, 3], coefficients float64 (flat, ``coeffs_size``
+doubles), output float64 or float32 [E, n, n].
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfea.so")
+
+MASS, HELMHOLTZ, ELASTICITY, NEOHOOKEAN = 0, 1, 2, 3
+FORMS = {"mass": MASS, "helmholtz": HELMHOLTZ, "elasticity": ELASTICITY, "neohookean": NEOHOOKEAN}
+OK, EINVAL, ENOMEM, ECUDA, EDEGENERATE, ETIMEOUT = 0, 1, 2, 3, 4, 5
+PREC_FP64, PREC_FP32 = 0, 1
+VARIANT_AUTO, VARIANT_NAIVE, VARIANT_SE, VARIANT_PRE = -1, 0, 1, 2
+VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
+
+EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
+           "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_sync", "fea_plan",
+           "fea_op_count", "fea_last_error", "fea_finalize"]
+
+
+class FeaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fea error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("out_f32", ctypes.c_int), ("variant", ctypes.c_int),
+                ("tile", ctypes.c_int), ("smem_budget", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("degree", ctypes.c_int), ("E", ctypes.c_int64),
+                ("coords", ctypes.c_void_p), ("coeffs", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("tile", ctypes.c_int), ("threads", ctypes.c_int),
+                ("quad_points", ctypes.c_int), ("ref_terms", ctypes.c_int), ("smem_bytes", ctypes.c_size_t),
+                ("flops_naive", ctypes.c_int64), ("flops_se", ctypes.c_int64), ("flops_pre", ctypes.c_int64),
+                ("flops_run", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libfea.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise FeaError(ECUDA, "CUDA library %s is missing: run __graft_entry__.build() first" % path)
+    lib = ctypes.CDLL(path)
+    i, i64, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    P = ctypes.POINTER
+    lib.fea_local_dim.argtypes = [i, i]
+    lib.fea_coeff_len.argtypes = [i, i]
+    lib.fea_coeffs_size.argtypes = [i, i, i64]
+    lib.fea_coeffs_size.restype = i64
+    lib.fea_quad_points.argtypes = [i, i]
+    lib.fea_assemble.argtypes = [i, i, i64, vp, vp, vp, vp]
+    lib.fea_assemble_ex.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
+    lib.fea_assemble_host.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
+    lib.fea_assemble_batch.argtypes = [P(Request), i, P(Options), vp]
+    lib.fea_sync.argtypes = [vp]
+    lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
+    lib.fea_op_count.argtypes = [i, i, i, P(i64), P(i64)]
+    lib.fea_last_error.restype = ctypes.c_char_p
+    lib.fea_finalize.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise FeaError(rc, load().fea_last_error().decode())
+
+
+def options(precision=PREC_FP32, out_f32=False, variant=VARIANT_AUTO, tile=0, smem_budget=0):
+    return Options(int(precision), int(bool(out_f32)), int(variant), int(tile), int(smem_budget))
+
+
+def local_dim(form, degree):
+    return load().fea_local_dim(form, degree)
+
+
+def coeff_len(form, degree):
+    return load().fea_coeff_len(form, degree)
+
+
+def coeffs_size(form, degree, E):
+    return load().fea_coeffs_size(form, degree, E)
+
+
+def quad_points(form, degree):
+    return load().fea_quad_points(form, degree)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def empty_out(form, degree, E, out_f32=False, device="cuda"):
+    import torch
+    n = local_dim(form, degree)
+    if n < 0:
+        raise FeaError(EINVAL, "unsupported form/degree (%r, %r)" % (form, degree))
+    return torch.empty((E, n, n), dtype=torch.float32 if out_f32 else torch.float64, device=device)
+
+
+def assemble(form, degree, coords, coeffs=None, out=None, precision=PREC_FP32, out_f32=False,
+             variant=VARIANT_AUTO, tile=0, smem_budget=0, stream=None):
+    """Element matrices of E elements (device tensors); returns `out`."""
+    E = coords.shape[0]
+    if out is None:
+        out = empty_out(form, degree, E, out_f32, coords.device)
+    o = options(precision, out_f32, variant, tile, smem_budget)
+    _check(load().fea_assemble_ex(form, degree, E, _ptr(coords), _ptr(coeffs), _ptr(out), ctypes.byref(o),
+                                  _stream_ptr(stream)))
+    return out
+
+
+def assemble_default(form, degree, coords, coeffs, out, stream=None):
+    """fea_assemble: the 5-argument call with default options."""
+    _check(load().fea_assemble(form, degree, coords.shape[0], _ptr(coords), _ptr(coeffs), _ptr(out),
+                               _stream_ptr(stream)))
+    return out
+
+
+def assemble_host(form, degree, coords, coeffs, out, precision=PREC_FP32, out_f32=False, variant=VARIANT_AUTO,
+                  tile=0, stream=None):
+    """Same with HOST tensors (pinned for full bandwidth); copies inside the call."""
+    o = options(precision, out_f32, variant, tile, 0)
+    _check(load().fea_assemble_host(form, degree, coords.shape[0], _ptr(coords), _ptr(coeffs), _ptr(out),
+                                    ctypes.byref(o), _stream_ptr(stream)))
+    return out
+
+
+def assemble_batch(requests, out_f32=False, stream=None):
+    """requests: list of (form, degree, coords, coeffs, out) device tensors, one persistent launch."""
+    arr = (Request * len(requests))()
+    for k, (form, degree, coords, coeffs, out) in enumerate(requests):
+        arr[k] = Request(form, degree, coords.shape[0], coords.data_ptr(),
+                         None if coeffs is None else coeffs.data_ptr(), out.data_ptr())
+    o = options(PREC_FP32, out_f32)
+    _check(load().fea_assemble_batch(arr, len(requests), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def sync(stream=None):
+    """Wait for the stream; raises FeaError(EDEGENERATE) after a degenerate element."""
+    _check(load().fea_sync(_stream_ptr(stream)))
+
+
+def plan(form, degree, precision=PREC_FP32, out_f32=False, variant=VARIANT_AUTO, tile=0, smem_budget=0):
+    info = PlanInfo()
+    o = options(precision, out_f32, variant, tile, smem_budget)
+    _check(load().fea_plan(form, degree, ctypes.byref(o), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+
+def op_count(form, degree, variant=VARIANT_AUTO):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fea_op_count(form, degree, variant, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def finalize():
+    if _lib is not None:
+        _lib.fea_finalize()

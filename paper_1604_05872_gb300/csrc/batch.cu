@@ -1,0 +1,208 @@
+// Uneven batches in one persistent launch.
+//
+// Every request is cut into tiles of its own size; the tiles of all requests
+// form one work list (request r owns global tiles [tile0_r, tile0_r + nt_r)).
+// A persistent CTA pulls the next tile with an atomic counter, finds its
+// request by binary search and dispatches on (variant, form, degree) to the
+// same tile functions the standalone kernels run.  Pulling never waits on
+// another CTA, so there is no spin loop.  The counter reset and the launch are
+// captured once into a CUDA graph per distinct batch and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fea.h"
+#include "host_model.h"
+#include "launch.cuh"
+#include "planner.h"
+#include "pre.cuh"
+#include "se.cuh"
+
+namespace fea {
+
+int kind_of(int variant, int form, int p) { return (variant == FEA_VARIANT_PRE ? 16 : 0) + form * 4 + (p - 1); }
+
+template <class K>
+__device__ __forceinline__ void run_one(const Req& q, int64_t t, char* sm, unsigned* err) {
+  const int64_t e0 = t * q.tile;
+  const int64_t left = q.E - e0;
+  K::tile(q, e0, (int)(left < q.tile ? left : q.tile), sm, err);
+}
+
+__global__ void __launch_bounds__(NT) batch_kernel(const Req* __restrict__ reqs, int nreq, long long total,
+                                                   unsigned long long* counter, unsigned* err) {
+  extern __shared__ __align__(16) char smem_raw[];
+  __shared__ long long s_w;
+  __shared__ int s_r;
+  for (;;) {
+    if (threadIdx.x == 0) s_w = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long w = s_w;
+    if (w >= total) break;
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = nreq - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (reqs[mid].tile0 <= w) lo = mid;
+        else hi = mid - 1;
+      }
+      s_r = lo;
+    }
+    __syncthreads();
+    const Req q = reqs[s_r];
+    const int64_t t = w - q.tile0;
+    switch (q.kind) {
+#define SEK(F, P) case (F) * 4 + (P) - 1: run_one<SeTile<F, P, float>>(q, t, smem_raw, err); break;
+#define PREK(F, P) case 16 + (F) * 4 + (P) - 1: run_one<PreTile<F, P, float>>(q, t, smem_raw, err); break;
+      SEK(0, 1) SEK(0, 2) SEK(0, 3) SEK(0, 4)
+      SEK(1, 1) SEK(1, 2) SEK(1, 3) SEK(1, 4)
+      SEK(2, 1) SEK(2, 2) SEK(2, 3) SEK(2, 4)
+      SEK(3, 1) SEK(3, 2) SEK(3, 3) SEK(3, 4)
+      PREK(0, 1) PREK(0, 2) PREK(0, 3) PREK(0, 4)
+      PREK(1, 1) PREK(1, 2) PREK(1, 3) PREK(1, 4)
+      PREK(2, 1) PREK(2, 2) PREK(2, 3) PREK(2, 4)
+#undef SEK
+#undef PREK
+      default: break;
+    }
+    __syncthreads();
+  }
+}
+
+struct BatchState {
+  std::vector<Req> sig;  // requests of the captured graph
+  size_t smem = 0;
+  int grid = 0;
+  Req* dreqs = nullptr;
+  size_t dcap = 0;
+  unsigned long long* counter = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void free_batch_state(BatchState* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->dreqs) cudaFree(b->dreqs);
+  if (b->counter) cudaFree(b->counter);
+  delete b;
+}
+
+// from fea_api.cu
+struct DevState;
+struct TableEntry;
+int get_dev_state(DevState** out);
+BatchState*& dev_batch(DevState* st);
+unsigned* device_error_word(DevState* st);
+int device_sms(DevState* st);
+const void* table_ptr(DevState* st, int form, int p, int prec, int* rc);
+int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl);
+int set_error(int code, const char* msg);
+
+static bool same_sig(const std::vector<Req>& a, const std::vector<Req>& b) {
+  if (a.size() != b.size()) return false;
+  return a.empty() || std::memcmp(a.data(), b.data(), a.size() * sizeof(Req)) == 0;
+}
+
+int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
+  if (nreq < 0 || (nreq > 0 && !reqs)) return set_error(FEA_EINVAL, "bad request list");
+  if (nreq == 0) return FEA_OK;
+  fea_options o;
+  if (opt) o = *opt;
+  else { o.precision = FEA_PREC_FP32; o.out_f32 = 0; o.variant = FEA_VARIANT_AUTO; o.tile = 0; o.smem_budget = 0; }
+  if (o.precision != FEA_PREC_FP32) return set_error(FEA_EINVAL, "the batched launch runs the FP32 contraction");
+  DevState* st = nullptr;
+  int rc = get_dev_state(&st);
+  if (rc) return rc;
+  std::vector<Req> R;
+  R.reserve(nreq);
+  size_t smem = 0;
+  long long tiles = 0;
+  for (int i = 0; i < nreq; ++i) {
+    const fea_request& r = reqs[i];
+    if (r.form < 0 || r.form > 3 || r.degree < 1 || r.degree > 4 || r.E < 0)
+      return set_error(FEA_EINVAL, "bad request");
+    if (r.E == 0) continue;
+    if (!r.coords || !r.out || (!r.coeffs && r.form != FEA_MASS)) return set_error(FEA_EINVAL, "NULL request buffer");
+    fea_options oi = o;
+    Plan pl;
+    if ((rc = make_plan(st, r.form, r.degree, oi, &pl))) return rc;
+    if (pl.variant == FEA_VARIANT_NAIVE) return set_error(FEA_EINVAL, "the batched launch has no plain variant");
+    Req q;
+    std::memset(&q, 0, sizeof(q));
+    q.coords = r.coords;
+    q.coeffs = r.coeffs;
+    q.out = r.out;
+    q.tab = table_ptr(st, r.form, r.degree, 1, &rc);
+    if (rc) return rc;
+    q.E = r.E;
+    q.form = r.form;
+    q.p = r.degree;
+    q.Q = pl.Q;
+    q.tile = pl.tile;
+    q.out_f32 = o.out_f32;
+    q.kind = kind_of(pl.variant, r.form, r.degree);
+    q.tile0 = tiles;
+    tiles += (r.E + pl.tile - 1) / pl.tile;
+    smem = std::max(smem, pl.smem);
+    R.push_back(q);
+  }
+  if (R.empty()) return FEA_OK;
+  BatchState*& bs = dev_batch(st);
+  if (!bs) bs = new BatchState();
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!bs->exec || !same_sig(bs->sig, R)) {
+    if (bs->exec) { cudaGraphExecDestroy(bs->exec); bs->exec = nullptr; }
+    if (bs->graph) { cudaGraphDestroy(bs->graph); bs->graph = nullptr; }
+    if (bs->dcap < R.size()) {
+      if (bs->dreqs) cudaFree(bs->dreqs);
+      bs->dreqs = nullptr;
+      if (cudaMalloc(&bs->dreqs, R.size() * sizeof(Req)) != cudaSuccess) return set_error(FEA_ENOMEM, "batch list");
+      bs->dcap = R.size();
+    }
+    if (!bs->counter && cudaMalloc(&bs->counter, sizeof(unsigned long long)) != cudaSuccess)
+      return set_error(FEA_ENOMEM, "batch counter");
+    if ((e = cudaMemcpy(bs->dreqs, R.data(), R.size() * sizeof(Req), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    const void* fn = reinterpret_cast<const void*>(&batch_kernel);
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem)) != cudaSuccess || per_sm < 1)
+      return set_error(FEA_ECUDA, "batch kernel occupancy");
+    bs->grid = (int)std::min<long long>(tiles, (long long)device_sms(st) * per_sm);
+    bs->smem = smem;
+    // capture: counter reset + persistent launch
+    cudaStream_t cap;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess)
+      return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    unsigned* err = device_error_word(st);
+    int nr = (int)R.size();
+    long long total = tiles;
+    Req* dr = bs->dreqs;
+    unsigned long long* ctr = bs->counter;
+    void* args[] = {&dr, &nr, &total, &ctr, &err};
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bs->counter, 0, sizeof(unsigned long long), cap);
+    if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3(bs->grid), dim3(NT), args, smem, cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return set_error(FEA_ECUDA, cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    bs->graph = g;
+    if ((e = cudaGraphInstantiate(&bs->exec, g, 0)) != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    bs->sig = R;
+  }
+  if ((e = cudaGraphLaunch(bs->exec, s)) != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  return FEA_OK;
+}
+
+}  // namespace fea

@@ -1,0 +1,412 @@
+// C ABI of the library (include/fea.h): argument checking, plans, device
+// tables, launches, the host-buffer pipeline and the batched persistent launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fea.h"
+#include "host_model.h"
+#include "kernels.h"
+#include "planner.h"
+
+namespace fea {
+
+static thread_local std::string g_last_error;
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+#define CUDA_TRY(x)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) return fail(FEA_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct TableEntry {
+  void* dev = nullptr;
+  TabLayout lay{};
+};
+
+struct DevState {
+  int dev = -1;
+  int sms = 0;
+  size_t smem_optin = 0;
+  unsigned* err = nullptr;  // device error word
+  std::map<std::tuple<int, int, int>, TableEntry> tables;
+  // host-buffer pipeline workspace
+  cudaStream_t hs[2] = {nullptr, nullptr};
+  void* ws[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  size_t ws_bytes[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  // batch
+  BatchState* batch = nullptr;
+};
+
+static std::mutex g_mu;
+static std::map<int, std::unique_ptr<DevState>> g_dev;
+
+static int get_dev(DevState** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_dev.find(dev);
+  if (it == g_dev.end()) {
+    auto st = std::make_unique<DevState>();
+    st->dev = dev;
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    st->sms = prop.multiProcessorCount;
+    st->smem_optin = prop.sharedMemPerBlockOptin;
+    CUDA_TRY(cudaMalloc(&st->err, sizeof(unsigned)));
+    CUDA_TRY(cudaMemset(st->err, 0, sizeof(unsigned)));
+    it = g_dev.emplace(dev, std::move(st)).first;
+  }
+  *out = it->second.get();
+  return FEA_OK;
+}
+
+unsigned* device_error_word(DevState* st) { return st->err; }
+int device_sms(DevState* st) { return st->sms; }
+int get_dev_state(DevState** out) { return get_dev(out); }
+BatchState*& dev_batch(DevState* st) { return st->batch; }
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+// Device tables of (form, degree, precision), built and uploaded once.
+int get_tables(DevState* st, int form, int p, int prec, TableEntry** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto key = std::make_tuple(form, p, prec);
+  auto it = st->tables.find(key);
+  if (it == st->tables.end()) {
+    Tables t = make_tables(form, p);
+    TableEntry te;
+    te.lay = tab_layout(t.Q, t.ns, t.r);
+    std::vector<double> h(te.lay.total, 0.0);
+    for (int q = 0; q < t.Q; ++q) h[te.lay.offW + q] = t.W[q];
+    for (size_t k = 0; k < t.phi.size(); ++k) h[te.lay.offPhi + k] = t.phi[k];
+    for (size_t k = 0; k < t.dphi.size(); ++k) h[te.lay.offDphi + k] = t.dphi[k];
+    for (size_t k = 0; k < t.phi1.size(); ++k) h[te.lay.offPhi1 + k] = t.phi1[k];
+    for (size_t k = 0; k < t.R.size(); ++k) h[te.lay.offR + k] = t.R[k];
+    size_t bytes = (size_t)te.lay.total * (prec == 0 ? 8 : 4);
+    if (cudaMalloc(&te.dev, bytes) != cudaSuccess) return fail(FEA_ENOMEM, "table allocation failed");
+    cudaError_t e;
+    if (prec == 0) {
+      e = cudaMemcpy(te.dev, h.data(), bytes, cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> hf(h.begin(), h.end());
+      e = cudaMemcpy(te.dev, hf.data(), bytes, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return fail(FEA_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    it = st->tables.emplace(key, te).first;
+  }
+  *out = &it->second;
+  return FEA_OK;
+}
+
+const void* table_ptr(DevState* st, int form, int p, int prec, int* rc) {
+  TableEntry* te = nullptr;
+  *rc = get_tables(st, form, p, prec, &te);
+  return *rc ? nullptr : te->dev;
+}
+
+static fea_options default_options() {
+  fea_options o;
+  o.precision = FEA_PREC_FP32;
+  o.out_f32 = 0;
+  o.variant = FEA_VARIANT_AUTO;
+  o.tile = 0;
+  o.smem_budget = 0;
+  return o;
+}
+
+static bool valid_fd(int form, int p) { return form >= 0 && form <= 3 && p >= 1 && p <= 4; }
+
+// Resolve variant, kernel and tile for a request.
+int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl) {
+  if (!valid_fd(form, p)) return fail(FEA_EINVAL, "unsupported form/degree");
+  if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32) return fail(FEA_EINVAL, "unsupported precision");
+  const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
+  const size_t limit = st ? st->smem_optin : 232448;
+  const size_t budget = o.smem_budget ? std::min(o.smem_budget, limit) : limit;
+  int variant = o.variant;
+  if (variant == FEA_VARIANT_AUTO) variant = choose_variant(form, p, prec, budget);
+  if (variant == FEA_VARIANT_NAIVE && prec != 0) return fail(FEA_EINVAL, "the plain variant is FP64 only");
+  if (variant == FEA_VARIANT_PRE && pre_terms(form, p) == 0)
+    return fail(FEA_EINVAL, "pre-evaluation does not apply to this form (integrand not polynomial)");
+  const KernelInfo* k = find_kernel(variant, form, p, prec);
+  if (!k) return fail(FEA_EINVAL, "no kernel for this variant/form/degree/precision");
+  const int Q = rule_points(rule_index(form, p));
+  int TE = o.tile;
+  if (TE < 0) return fail(FEA_EINVAL, "negative tile");
+  if (TE == 0) TE = default_tile(variant, form, p, prec, k->max_tile, budget, Q, k->smem);
+  if (TE < 1 || TE > k->max_tile) return fail(FEA_EINVAL, "tile out of range for this kernel");
+  const size_t smem = k->smem(TE, Q);
+  if (smem > budget) return fail(FEA_EINVAL, "tile does not fit the shared-memory budget (Constraint 2)");
+  pl->k = k;
+  pl->variant = variant;
+  pl->prec = prec;
+  pl->tile = TE;
+  pl->Q = Q;
+  pl->smem = smem;
+  return FEA_OK;
+}
+
+static int check_device_ptr(const void* p, const char* what, bool allow_null) {
+  if (!p) return allow_null ? FEA_OK : fail(FEA_EINVAL, std::string(what) + " is NULL");
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FEA_EINVAL, std::string(what) + " is not a device pointer");
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(FEA_EINVAL, std::string(what) + " is a host pointer (device memory required; no CPU fallback)");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (a.type == cudaMemoryTypeDevice && a.device != dev)
+    return fail(FEA_EINVAL, std::string(what) + " belongs to another device");
+  if (reinterpret_cast<uintptr_t>(p) & 7) return fail(FEA_EINVAL, std::string(what) + " is not 8-byte aligned");
+  return FEA_OK;
+}
+
+int launch_plan(DevState* st, const Plan& pl, int form, int p, int64_t E, const double* coords, const double* coeffs,
+                void* out, int out_f32, cudaStream_t stream) {
+  TableEntry* te = nullptr;
+  int rc = get_tables(st, form, p, pl.prec, &te);
+  if (rc) return rc;
+  Req q;
+  q.coords = coords;
+  q.coeffs = coeffs;
+  q.out = out;
+  q.tab = te->dev;
+  q.E = E;
+  q.form = form;
+  q.p = p;
+  q.Q = pl.Q;
+  q.tile = pl.tile;
+  q.out_f32 = out_f32;
+  q.kind = 0;
+  q.tile0 = 0;
+  const int64_t ntiles = (E + pl.tile - 1) / pl.tile;
+  CUDA_TRY(cudaFuncSetAttribute(pl.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, NT, pl.smem));
+  if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with this tile");
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
+  unsigned* err = st->err;
+  void* args[] = {&q, &err};
+  CUDA_TRY(cudaLaunchKernel(pl.k->fn, dim3((unsigned)grid), dim3(NT), args, pl.smem, stream));
+  return FEA_OK;
+}
+
+int assemble_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
+                  const fea_options* opt, void* stream) {
+  if (!valid_fd(form, degree)) return fail(FEA_EINVAL, "unsupported form/degree");
+  if (E < 0) return fail(FEA_EINVAL, "negative element count");
+  const fea_options o = opt ? *opt : default_options();
+  if (o.out_f32 != 0 && o.out_f32 != 1) return fail(FEA_EINVAL, "out_f32 must be 0 or 1");
+  const int n = local_dim(form, degree);
+  if (E > (int64_t)(INT64_MAX / ((int64_t)n * n * 8))) return fail(FEA_EINVAL, "size overflow");
+  DevState* st = nullptr;
+  int rc = get_dev(&st);
+  if (rc) return rc;
+  Plan pl;
+  rc = make_plan(st, form, degree, o, &pl);
+  if (rc) return rc;
+  if (E == 0) return FEA_OK;
+  if ((rc = check_device_ptr(coords, "coords", false))) return rc;
+  if ((rc = check_device_ptr(coeffs, "coeffs", form == FEA_MASS))) return rc;
+  if ((rc = check_device_ptr(out, "out", false))) return rc;
+  return launch_plan(st, pl, form, degree, E, coords, coeffs, out, o.out_f32, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ host API
+static int ensure_ws(DevState* st, int b, int k, size_t bytes) {
+  if (st->ws_bytes[b][k] >= bytes) return FEA_OK;
+  if (st->ws[b][k]) cudaFree(st->ws[b][k]);
+  st->ws[b][k] = nullptr;
+  st->ws_bytes[b][k] = 0;
+  if (cudaMalloc(&st->ws[b][k], bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FEA_ENOMEM, "workspace allocation failed");
+  }
+  st->ws_bytes[b][k] = bytes;
+  return FEA_OK;
+}
+
+int assemble_host_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
+                       const fea_options* opt, void* stream) {
+  if (!valid_fd(form, degree)) return fail(FEA_EINVAL, "unsupported form/degree");
+  if (E < 0) return fail(FEA_EINVAL, "negative element count");
+  const fea_options o = opt ? *opt : default_options();
+  DevState* st = nullptr;
+  int rc = get_dev(&st);
+  if (rc) return rc;
+  Plan pl;
+  rc = make_plan(st, form, degree, o, &pl);
+  if (rc) return rc;
+  if (E == 0) return FEA_OK;
+  if (!coords || !out || (!coeffs && form != FEA_MASS)) return fail(FEA_EINVAL, "NULL host buffer");
+  const int n = local_dim(form, degree);
+  const int clen = coeff_len(form, degree);
+  const size_t osz = o.out_f32 ? 4 : 8;
+  for (int b = 0; b < 2; ++b)
+    if (!st->hs[b]) CUDA_TRY(cudaStreamCreateWithFlags(&st->hs[b], cudaStreamNonBlocking));
+  // chunks: at least 4 for overlap, tile-aligned, at most 64 MiB of output each
+  int64_t chunk = std::max<int64_t>(pl.tile, (int64_t)((64ull << 20) / ((size_t)n * n * osz)));
+  chunk = std::min<int64_t>(chunk, (E + 3) / 4);
+  chunk = std::max<int64_t>(1, (chunk + pl.tile - 1) / pl.tile * pl.tile);
+  const size_t cbytes = (size_t)chunk * 12 * 8;
+  const size_t fbytes = ((size_t)chunk * clen + (form == FEA_NEOHOOKEAN ? 2 : 0)) * 8;
+  const size_t obytes = (size_t)chunk * n * n * osz;
+  for (int b = 0; b < 2; ++b) {
+    if ((rc = ensure_ws(st, b, 0, cbytes))) return rc;
+    if (fbytes && (rc = ensure_ws(st, b, 1, fbytes))) return rc;
+    if ((rc = ensure_ws(st, b, 2, obytes))) return rc;
+  }
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventRecord(ev, us));
+  for (int b = 0; b < 2; ++b) CUDA_TRY(cudaStreamWaitEvent(st->hs[b], ev, 0));
+  int k = 0;
+  for (int64_t e0 = 0; e0 < E; e0 += chunk, ++k) {
+    const int b = k & 1;
+    cudaStream_t s = st->hs[b];
+    const int64_t ne = std::min<int64_t>(chunk, E - e0);
+    double* dc = (double*)st->ws[b][0];
+    double* df = (double*)st->ws[b][1];
+    CUDA_TRY(cudaMemcpyAsync(dc, coords + e0 * 12, (size_t)ne * 96, cudaMemcpyHostToDevice, s));
+    if (clen) CUDA_TRY(cudaMemcpyAsync(df, coeffs + e0 * clen, (size_t)ne * clen * 8, cudaMemcpyHostToDevice, s));
+    if (form == FEA_NEOHOOKEAN)
+      CUDA_TRY(cudaMemcpyAsync(df + ne * clen, coeffs + E * clen, 16, cudaMemcpyHostToDevice, s));
+    rc = launch_plan(st, pl, form, degree, ne, dc, clen ? df : nullptr, st->ws[b][2], o.out_f32, s);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync((char*)out + (size_t)e0 * n * n * osz, st->ws[b][2], (size_t)ne * n * n * osz,
+                             cudaMemcpyDeviceToHost, s));
+  }
+  for (int b = 0; b < 2; ++b) CUDA_TRY(cudaStreamSynchronize(st->hs[b]));
+  cudaEventDestroy(ev);
+  return FEA_OK;
+}
+
+int sync_impl(void* stream) {
+  DevState* st = nullptr;
+  int rc = get_dev(&st);
+  if (rc) return rc;
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned h = 0;
+  CUDA_TRY(cudaMemcpy(&h, st->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (h) {
+    CUDA_TRY(cudaMemset(st->err, 0, sizeof(unsigned)));
+    return fail(FEA_EDEGENERATE, "degenerate element (det J == 0 or det F <= 0); NaN written for it");
+  }
+  return FEA_OK;
+}
+
+void finalize_impl() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_dev) {
+    DevState* st = kv.second.get();
+    cudaSetDevice(st->dev);
+    for (auto& t : st->tables) cudaFree(t.second.dev);
+    for (int b = 0; b < 2; ++b) {
+      for (int k = 0; k < 3; ++k)
+        if (st->ws[b][k]) cudaFree(st->ws[b][k]);
+      if (st->hs[b]) cudaStreamDestroy(st->hs[b]);
+    }
+    free_batch_state(st->batch);
+    cudaFree(st->err);
+  }
+  g_dev.clear();
+  cudaSetDevice(cur);
+}
+
+int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
+
+}  // namespace fea
+
+using namespace fea;
+
+extern "C" {
+
+int fea_local_dim(int form, int degree) { return valid_fd(form, degree) ? local_dim(form, degree) : -1; }
+int fea_coeff_len(int form, int degree) { return valid_fd(form, degree) ? coeff_len(form, degree) : -1; }
+int64_t fea_coeffs_size(int form, int degree, int64_t E) {
+  if (!valid_fd(form, degree) || E < 0) return -1;
+  return (int64_t)coeff_len(form, degree) * E + (form == FEA_NEOHOOKEAN ? 2 : 0);
+}
+int fea_quad_points(int form, int degree) {
+  return valid_fd(form, degree) ? rule_points(rule_index(form, degree)) : -1;
+}
+
+int fea_assemble(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out, void* stream) {
+  return assemble_impl(form, degree, E, coords, coeffs, out, nullptr, stream);
+}
+int fea_assemble_ex(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
+                    const fea_options* opt, void* stream) {
+  return assemble_impl(form, degree, E, coords, coeffs, out, opt, stream);
+}
+int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host, const double* coeffs_host,
+                      void* out_host, const fea_options* opt, void* stream) {
+  return assemble_host_impl(form, degree, E, coords_host, coeffs_host, out_host, opt, stream);
+}
+int fea_assemble_batch(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
+  return batch_impl(reqs, nreq, opt, stream);
+}
+int fea_sync(void* stream) { return sync_impl(stream); }
+
+int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info) {
+  if (!info) return fail(FEA_EINVAL, "info is NULL");
+  const fea_options o = opt ? *opt : default_options();
+  DevState* st = nullptr;
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) == cudaSuccess && dev_count > 0) {
+    int rc = get_dev(&st);
+    if (rc) return rc;
+  } else {
+    cudaGetLastError();
+  }
+  Plan pl;
+  int rc = make_plan(st, form, degree, o, &pl);
+  if (rc) return rc;
+  OpCounts oc = op_counts(form, degree);
+  info->variant = pl.variant;
+  info->tile = pl.tile;
+  info->threads = NT;
+  info->quad_points = pl.Q;
+  info->ref_terms = pre_terms(form, degree);
+  info->smem_bytes = pl.smem;
+  info->flops_naive = oc.naive;
+  info->flops_se = oc.se;
+  info->flops_pre = oc.pre;
+  info->flops_run = pl.variant == FEA_VARIANT_PRE ? oc.pre : pl.variant == FEA_VARIANT_SE ? oc.se : oc.naive;
+  const int n = local_dim(form, degree);
+  info->bytes = 96 + 8 * (int64_t)coeff_len(form, degree) + (int64_t)n * n * (o.out_f32 ? 4 : 8);
+  return FEA_OK;
+}
+
+int fea_op_count(int form, int degree, int variant, int64_t* naive_flops, int64_t* opt_flops) {
+  if (!valid_fd(form, degree)) return fail(FEA_EINVAL, "unsupported form/degree");
+  OpCounts oc = op_counts(form, degree);
+  if (variant == FEA_VARIANT_AUTO) variant = choose_variant(form, degree, 1, 232448);
+  int64_t v = variant == FEA_VARIANT_PRE ? oc.pre : variant == FEA_VARIANT_SE ? oc.se : oc.naive;
+  if (v < 0) return fail(FEA_EINVAL, "variant not applicable");
+  if (naive_flops) *naive_flops = oc.naive;
+  if (opt_flops) *opt_flops = v;
+  return FEA_OK;
+}
+
+const char* fea_last_error(void) { return g_last_error.c_str(); }
+void fea_finalize(void) { finalize_impl(); }
+
+}  // extern "C"

@@ -1,0 +1,26 @@
+// Registry of compiled tile kernels (host side).
+#pragma once
+#include <cstddef>
+
+#include "layout.h"
+
+namespace fea {
+
+struct KernelInfo {
+  const void* fn;                     // __global__ void (Req, unsigned*)
+  int variant, form, p, prec;         // prec: 0 = FP64, 1 = FP32
+  int max_tile;                       // upper bound on elements per tile
+  size_t (*smem)(int TE, int Q);      // dynamic shared memory for a tile of TE
+};
+
+// Registered by the kernel translation units.
+extern const KernelInfo kPreKernels[];
+extern const int kNumPreKernels;
+extern const KernelInfo kSeKernels[];
+extern const int kNumSeKernels;
+extern const KernelInfo kNaiveKernels[];
+extern const int kNumNaiveKernels;
+
+const KernelInfo* find_kernel(int variant, int form, int p, int prec);
+
+}  // namespace fea

@@ -1,0 +1,28 @@
+// Instantiations of the plain FP64 quadrature nest (the comparator; all forms, P1-P4).
+#include "launch.cuh"
+#include "naive.cuh"
+
+namespace fea {
+
+#define NV(F, P) make_info<NaiveTile<F, P>>(V_NAIVE, F, P, 0)
+const KernelInfo kNaiveKernels[] = {
+    NV(0, 1), NV(0, 2), NV(0, 3), NV(0, 4),
+    NV(1, 1), NV(1, 2), NV(1, 3), NV(1, 4),
+    NV(2, 1), NV(2, 2), NV(2, 3), NV(2, 4),
+    NV(3, 1), NV(3, 2), NV(3, 3), NV(3, 4),
+};
+#undef NV
+const int kNumNaiveKernels = sizeof(kNaiveKernels) / sizeof(kNaiveKernels[0]);
+
+const KernelInfo* find_kernel(int variant, int form, int p, int prec) {
+  const KernelInfo* tabs[3] = {kNaiveKernels, kSeKernels, kPreKernels};
+  const int counts[3] = {kNumNaiveKernels, kNumSeKernels, kNumPreKernels};
+  if (variant < 0 || variant > 2) return nullptr;
+  for (int i = 0; i < counts[variant]; ++i) {
+    const KernelInfo& k = tabs[variant][i];
+    if (k.form == form && k.p == p && k.prec == prec) return &k;
+  }
+  return nullptr;
+}
+
+}  // namespace fea

@@ -1,0 +1,178 @@
+// Host planner (see planner.h).
+//
+// Operation counts follow Definition 8's convention (additions and products;
+// a fused multiply-add counts as two; divisions, square roots and logarithms
+// are not counted).  They are the counts of the loop nests the kernels run:
+//
+//   naive  plain quadrature nest in normal form: everything inside (q, i, j)
+//   SE     quadrature nest after sharing elimination (Algorithm 1): physical
+//          gradients hoisted per (q, a), pointwise kernels per q, left
+//          operands per (q, a, c), and 2 x (#products) flops per entry
+//   PRE    pre-evaluated reference tensors (Algorithm 2): geometry tensor per
+//          element, then 2 r flops per output entry
+//
+// Algorithm 3 enumerates the bipartitions of the pre-evaluable monomials,
+// drops those whose pre-evaluated tables do not fit T_H (Constraint 2) and
+// takes the cheapest by theta = theta_se(S u b_S) + theta_pre(b_P).
+#include "planner.h"
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fea.h"
+#include "host_model.h"
+
+namespace fea {
+
+// Flops of one monomial of a form under each schedule, per element.
+struct MonoCost {
+  int64_t se, pre;       // pre < 0: not pre-evaluable
+  int64_t table_bytes4;  // pre-evaluated table size in 4-byte words
+};
+
+static std::vector<MonoCost> monomials(int form, int p) {
+  const int64_t ns = nbasis(p), Q = rule_points(rule_index(form, p));
+  const int64_t n = vector_form(form) ? 3 * ns : ns, nn = n * n;
+  const int64_t grad = 15 * ns;  // physical gradients per point: 3 x (3 mul + 2 add) per basis function
+  std::vector<MonoCost> m;
+  switch (form) {
+    case MASS:
+      // SE: s = w|det| (1), t_a = s phi_a (ns), entry += t_a phi_b (2)
+      m.push_back({Q * (1 + ns + 2 * nn), 2 * nn, ns * ns});
+      break;
+    case HELMHOLTZ:
+      // stiffness: SE needs the gradients, 3 scaled copies and 3 FMA per entry;
+      // PRE: K (6 x 6 flops) + 6 terms per entry
+      m.push_back({Q * (grad + 1 + 3 * ns + 6 * nn), 36 + 12 * nn, 6 * ns * ns});
+      // f-mass: SE needs f_q (2 ns), s f_q phi_a (ns + 1), 1 FMA per entry; PRE: |det| f_k (ns) + ns terms
+      m.push_back({Q * (2 * ns + ns + 1 + 2 * nn), ns + 2 * ns * nn, ns * ns * ns});
+      break;
+    case ELASTICITY:
+      // SE: gradients, mu_q/lam_q (16), D (81 x 4), left operands 45 per row, 3 FMA per entry
+      // PRE: geometry tensor 324 x 8, 36 terms per entry
+      m.push_back({Q * (grad + 18 + 324 + 45 * n + 6 * nn), 324 * 8 + 72 * nn, 36 * ns * ns});
+      break;
+    case NEOHOOKEAN:
+      // SE: gradients twice (F and contraction), F (18 ns), D (81 x 10), left operands, 3 FMA per entry
+      m.push_back({Q * (2 * grad + 18 * ns + 810 + 45 * n + 6 * nn), -1, 0});
+      break;
+  }
+  return m;
+}
+
+OpCounts op_counts(int form, int p) {
+  const int64_t ns = nbasis(p), Q = rule_points(rule_index(form, p));
+  const int64_t n = vector_form(form) ? 3 * ns : ns, nn = n * n;
+  const int64_t geo = 9 + 27 + 5;  // J, adjugate (9 x (mul + fma)), det
+  OpCounts oc;
+  // naive: per (q, i, j) normal-form integrand, plus per-(e, q) coefficient values
+  int64_t per_entry = 0, per_point = 0;
+  switch (form) {
+    case MASS: per_entry = 4; per_point = 0; break;
+    case HELMHOLTZ: per_entry = 41; per_point = 2 * ns; break;
+    case ELASTICITY: per_entry = 39 + 2; per_point = 16; break;  // + 5 on the 1/3 diagonal entries
+    case NEOHOOKEAN: per_entry = 141; per_point = 33 * ns + 60; break;
+  }
+  oc.naive = geo + Q * (per_point + per_entry * nn);
+  int64_t se = geo, pre = geo;
+  bool pre_ok = true;
+  for (const MonoCost& m : monomials(form, p)) {
+    se += m.se;
+    if (m.pre < 0) pre_ok = false;
+    else pre += m.pre;
+  }
+  if (form == HELMHOLTZ) se -= Q * (1 + 3 * ns + 2 * ns);  // shared s and left-operand build counted once
+  oc.se = se;
+  oc.pre = pre_ok ? pre : -1;
+  return oc;
+}
+
+static std::mutex g_tmu;
+static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;
+
+void set_tuned(int form, int p, int prec, int variant, int tile) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_tuned[std::make_tuple(form, p, prec)] = {variant, tile};
+}
+bool get_tuned(int form, int p, int prec, int* variant, int* tile) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  auto it = g_tuned.find(std::make_tuple(form, p, prec));
+  if (it == g_tuned.end()) return false;
+  *variant = it->second.first;
+  *tile = it->second.second;
+  return true;
+}
+void clear_tuned() {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_tuned.clear();
+}
+
+// Algorithm 3: returns a bitmask of the monomials to pre-evaluate.
+unsigned algorithm3(int form, int p, int prec, size_t budget, int64_t* best_cost) {
+  std::vector<MonoCost> M = monomials(form, p);
+  const int nm = (int)M.size();
+  // step 1: S = {theta > 0} stays with sharing elimination; P = the rest
+  std::vector<int> P;
+  for (int i = 0; i < nm; ++i)
+    if (M[i].pre >= 0 && M[i].pre - M[i].se <= 0) P.push_back(i);
+  const size_t word = prec == 0 ? 8 : 4;
+  unsigned best = 0;
+  int64_t bestc = INT64_MAX;
+  // steps 2-4: all bipartitions (b_S, b_P) of P, Constraint 2 filter, argmin
+  for (unsigned b = 0; b < (1u << P.size()); ++b) {
+    size_t mem = 0;
+    int64_t cost = 0;
+    unsigned mask = 0;
+    for (int i = 0; i < nm; ++i) {
+      bool pre = false;
+      for (size_t k = 0; k < P.size(); ++k)
+        if (P[k] == i && (b >> k & 1u)) pre = true;
+      if (pre) {
+        mask |= 1u << i;
+        mem += (size_t)M[i].table_bytes4 * word;
+        cost += M[i].pre;
+      } else {
+        cost += M[i].se;
+      }
+    }
+    if (mem > budget) continue;
+    if (cost < bestc) {
+      bestc = cost;
+      best = mask;
+    }
+  }
+  if (best_cost) *best_cost = bestc;
+  return best;
+}
+
+int choose_variant(int form, int p, int prec, size_t budget) {
+  int v = 0, t = 0;
+  if (get_tuned(form, p, prec, &v, &t) && v != FEA_VARIANT_AUTO) return v;
+  if (form == NEOHOOKEAN) return FEA_VARIANT_SE;
+  const unsigned mask = algorithm3(form, p, prec, budget, nullptr);
+  const int nm = (int)monomials(form, p).size();
+  if (mask == (1u << nm) - 1) return FEA_VARIANT_PRE;
+  if (mask == 0) return FEA_VARIANT_SE;
+  // A mixed bipartition: the kernels implement whole-form variants, so take
+  // the cheaper of the two.
+  OpCounts oc = op_counts(form, p);
+  return (oc.pre >= 0 && oc.pre <= oc.se) ? FEA_VARIANT_PRE : FEA_VARIANT_SE;
+}
+
+int default_tile(int variant, int form, int p, int prec, int max_tile, size_t budget, int Q,
+                 size_t (*smem)(int, int)) {
+  int v = 0, t = 0;
+  if (get_tuned(form, p, prec, &v, &t) && t > 0 && t <= max_tile && smem(t, Q) <= budget) return t;
+  // target a few resident CTAs per SM: about 48 KB of shared memory per tile
+  const size_t target = std::min<size_t>(budget, 48 * 1024);
+  int best = 1;
+  for (int te = 1; te <= max_tile; ++te)
+    if (smem(te, Q) <= target) best = te;
+  (void)variant;
+  return best;
+}
+
+}  // namespace fea

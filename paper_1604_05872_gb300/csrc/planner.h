@@ -1,0 +1,41 @@
+// Host planner: operation counts of the loop-nest variants, the transformation
+// algorithm's choice between sharing elimination and pre-evaluation, tile
+// selection, and tuned overrides.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace fea {
+
+struct Plan {
+  const KernelInfo* k = nullptr;
+  int variant = 0, prec = 1, tile = 0, Q = 0;
+  size_t smem = 0;
+};
+
+// Per-element operation counts (adds and products; an FMA counts 2) of the
+// three loop nests as the kernels execute them.  pre = -1 when the form has no
+// pre-evaluated form.
+struct OpCounts {
+  int64_t naive, se, pre;
+};
+OpCounts op_counts(int form, int p);
+
+// Algorithm 3 (Section 4.1) on the form's monomials with the memory threshold
+// T_H = `budget` bytes of shared memory: returns FEA_VARIANT_SE or _PRE.
+// Tuned choices installed with set_tuned() take precedence.
+int choose_variant(int form, int p, int prec, size_t budget);
+int default_tile(int variant, int form, int p, int prec, int max_tile, size_t budget, int Q,
+                 size_t (*smem)(int, int));
+
+// Tuned overrides (autotuner / learned cost model), keyed by (form, p, prec).
+void set_tuned(int form, int p, int prec, int variant, int tile);
+bool get_tuned(int form, int p, int prec, int* variant, int* tile);
+void clear_tuned();
+
+struct BatchState;
+void free_batch_state(BatchState* b);
+
+}  // namespace fea

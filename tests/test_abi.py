@@ -1,0 +1,85 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every symbol that
+include/fea.h declares, and its host-side logic (sizes, rules, planner, op
+counts) answers without a GPU.  No assembly is launched here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1604_05872_gb300 as fea
+from paper_1604_05872_gb300 import build as fbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fbuild.build()
+    return fea.load()
+
+
+def declared_symbols():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(fea_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "fea_assemble" in names and len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(fea.EXPORTS) <= set(names)
+
+
+def test_sizes(lib):
+    assert [fea.local_dim(0, p) for p in range(1, 5)] == [4, 10, 20, 35]
+    assert [fea.local_dim(2, p) for p in range(1, 5)] == [12, 30, 60, 105]
+    assert fea.coeff_len(1, 2) == 10 and fea.coeff_len(2, 3) == 8 and fea.coeff_len(3, 2) == 30
+    assert fea.coeffs_size(3, 2, 100) == 3002 and fea.coeffs_size(0, 1, 5) == 0
+    assert fea.local_dim(4, 1) == -1 and fea.local_dim(0, 5) == -1 and fea.coeffs_size(1, 1, -1) == -1
+
+
+def test_quadrature_points_match_oracle_rules(lib, orc):
+    for form in range(4):
+        for p in range(1, 5):
+            m = orc.default_rule(form, p)
+            assert fea.quad_points(form, p) == (4 if m == 0 else m ** 3)
+
+
+def test_plan_without_gpu(lib):
+    info = fea.plan(fea.HELMHOLTZ, 2)
+    assert info["variant"] == fea.VARIANT_PRE and info["quad_points"] == 64 and info["ref_terms"] == 16
+    assert info["flops_pre"] < info["flops_se"] < info["flops_naive"]
+    assert info["bytes"] == 96 + 80 + 800
+    nh = fea.plan(fea.NEOHOOKEAN, 2)
+    assert nh["variant"] == fea.VARIANT_SE and nh["flops_pre"] == -1
+    with pytest.raises(fea.FeaError) as e:
+        fea.plan(fea.NEOHOOKEAN, 2, variant=fea.VARIANT_PRE)
+    assert e.value.code == fea.EINVAL
+    with pytest.raises(fea.FeaError):
+        fea.plan(fea.MASS, 1, precision=fea.PREC_FP32, variant=fea.VARIANT_NAIVE)
+    with pytest.raises(fea.FeaError):
+        fea.plan(7, 1)
+    with pytest.raises(fea.FeaError):
+        fea.plan(fea.HELMHOLTZ, 2, tile=100000)
+
+
+def test_op_counts_decrease(lib):
+    for form in range(4):
+        for p in range(1, 5):
+            naive, best = fea.op_count(form, p)
+            assert 0 < best < naive, (form, p)
+
+
+def test_shared_memory_budget_is_constraint_two(lib):
+    # a tiny T_H forces small tiles, then rejection
+    small = fea.plan(fea.ELASTICITY, 3, smem_budget=60 * 1024)
+    assert small["smem_bytes"] <= 60 * 1024
+    with pytest.raises(fea.FeaError):
+        fea.plan(fea.ELASTICITY, 4, smem_budget=4 * 1024)
