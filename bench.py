@@ -70,55 +70,94 @@ def profiled_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
+    """SM clock and clock-event reasons sampled through NVML (libnvidia-ml,
+    read-only queries) by a background thread during the timed region, plus an
+    nvidia-smi log of the same quantities written beside the run."""
 
-    def __init__(self, index):
-        self.index = index
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index, period=0.002):
+        self.index, self.period = index, period
+        self.samples, self.max_mhz = [], None
+        self.nvml = None
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def _init_nvml(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                return False
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self.nvml, self.h = lib, h
+            return True
+        except OSError:
+            return False
+
+    def _run(self):
+        import ctypes
+        mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        get_r = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.h, ctypes.c_int(1), ctypes.byref(mhz)) == 0:
+                r = rs.value if get_r(self.h, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((mhz.value, r))
+            time.sleep(self.period)
 
     def __enter__(self):
+        import threading
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.log = open(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv"), "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv", "-lms", "200"], stdout=self.log, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        self.stop = threading.Event()
+        if self._init_nvml():
+            self.thread = threading.Thread(target=self._run, daemon=True)
+            self.thread.start()
+            t0 = time.time()
+            while not self.samples and time.time() - t0 < 2.0:
+                time.sleep(0.001)
+            self.samples.clear()
+        else:
+            self.thread = None
         return self
 
     def __exit__(self, *a):
+        self.stop.set()
+        if self.thread:
+            self.thread.join(timeout=2)
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-            self.f.close()
+            self.log.close()
 
     def summary(self):
-        if not self.proc:
+        if not self.samples:
             return None
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 7 and parts[0].isdigit():
-                rows.append(parts)
-        if not rows:
-            return None
-        sm = [int(r[0]) for r in rows]
         reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            for k, nm in enumerate(names):
-                if r[3 + k].lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": int(rows[0][1]), "reasons": sorted(reasons),
-                "samples": len(rows)}
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([m for m, _ in self.samples])), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml"}
 
 
 def make_inputs(E, seed_offset=0):

@@ -153,6 +153,42 @@ int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info);
  * FMA counts 2) of the plain nest and of `variant` (AUTO = Algorithm 3 pick). */
 int fea_op_count(int form, int degree, int variant, int64_t* naive_flops, int64_t* opt_flops);
 
+/* ---- the planner's operation-count algorithm (host only, no GPU needed) ----
+ * Expression language: program := stmt (';' stmt)*, stmt := loops ':' lhs
+ * ('=' | '+=') expr, loops := index (',' index)*, expr over + - * and
+ * parentheses, symbols name[i,j,...].  Extents: "e:1,i:64,j:10,k:10". */
+
+/* Operation count of a loop-nest program (Definition 8 with the convention of
+ * Figure "poisson": adds and products, '+=' counts one, a sub-expression that
+ * occurs more than once in one loop body is counted once). */
+int fea_opcount_program(const char* program, const char* extents, int64_t* ops);
+
+/* Algorithm 1 (sharing elimination, Section 3.2) on `lhs += expr` inside the
+ * loops (comma separated, outermost first; the last two are the linear
+ * test/trial loops).  Writes the transformed program (same language) into
+ * `program` (capacity `cap` bytes, may be NULL), its operation count and the
+ * size of the minimum vertex cover of the sharing graph (step 5's ILP). */
+int fea_sharing_elimination(const char* lhs, const char* expr, const char* loops, const char* extents,
+                            char* program, size_t cap, int64_t* ops, int* cover);
+
+/* Minimum vertex cover of a bipartite graph (the ILP of Algorithm 1, step 5):
+ * left vertices 0..nl-1, right 0..nr-1, edges[2k], edges[2k+1]. */
+int fea_vertex_cover(int nl, int nr, const int* edges, int nedges, int* cover_size);
+
+/* Increase factor iota = C(n + k - 1, k) of pre-evaluation (Section 4.2);
+ * -1 for n < 1 or k < 0. */
+int64_t fea_increase_factor(int n, int k);
+
+/* Monomials of a form (Section 2.1) and their costs per element: theta_se
+ * (Algorithm 1), theta_pre (rho * iota tables, Section 4.2; -1 when the
+ * integrand is not polynomial) and the pre-evaluated table size in words. */
+int fea_num_monomials(int form, int degree);
+int fea_theta(int form, int degree, int monomial, int64_t* theta_se, int64_t* theta_pre, int64_t* table_words);
+
+/* Algorithm 3 (Section 4.1): bitmask of the monomials to pre-evaluate under
+ * the memory threshold T_H = smem_budget bytes (0 = 227 KB), and its cost. */
+int fea_algorithm3(int form, int degree, int precision, size_t smem_budget, unsigned* premask, int64_t* cost);
+
 const char* fea_last_error(void);
 void fea_finalize(void);
 

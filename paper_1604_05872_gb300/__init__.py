@@ -24,7 +24,9 @@ VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_sync", "fea_plan",
-           "fea_op_count", "fea_last_error", "fea_finalize"]
+           "fea_op_count", "fea_opcount_program", "fea_sharing_elimination", "fea_vertex_cover",
+           "fea_increase_factor", "fea_num_monomials", "fea_theta", "fea_algorithm3",
+           "fea_last_error", "fea_finalize"]
 
 
 class FeaError(RuntimeError):
@@ -76,6 +78,15 @@ def load(path=None):
     lib.fea_sync.argtypes = [vp]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
     lib.fea_op_count.argtypes = [i, i, i, P(i64), P(i64)]
+    cp = ctypes.c_char_p
+    lib.fea_opcount_program.argtypes = [cp, cp, P(i64)]
+    lib.fea_sharing_elimination.argtypes = [cp, cp, cp, cp, ctypes.c_char_p, ctypes.c_size_t, P(i64), P(i)]
+    lib.fea_vertex_cover.argtypes = [i, i, P(i), i, P(i)]
+    lib.fea_increase_factor.argtypes = [i, i]
+    lib.fea_increase_factor.restype = i64
+    lib.fea_num_monomials.argtypes = [i, i]
+    lib.fea_theta.argtypes = [i, i, i, P(i64), P(i64), P(i64)]
+    lib.fea_algorithm3.argtypes = [i, i, i, ctypes.c_size_t, P(ctypes.c_uint), P(i64)]
     lib.fea_last_error.restype = ctypes.c_char_p
     lib.fea_finalize.argtypes = []
     _lib = lib
@@ -180,6 +191,56 @@ def op_count(form, degree, variant=VARIANT_AUTO):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().fea_op_count(form, degree, variant, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def opcount_program(program, extents):
+    """Operation count of a loop-nest program (see include/fea.h)."""
+    ops = ctypes.c_int64()
+    _check(load().fea_opcount_program(program.encode(), _ext(extents), ctypes.byref(ops)))
+    return ops.value
+
+
+def _ext(extents):
+    if isinstance(extents, dict):
+        extents = ",".join("%s:%d" % kv for kv in extents.items())
+    return extents.encode()
+
+
+def sharing_elimination(lhs, expr, loops, extents):
+    """Algorithm 1 on `lhs += expr`: (program text, operation count, vertex-cover size)."""
+    buf = ctypes.create_string_buffer(1 << 20)
+    ops, cover = ctypes.c_int64(), ctypes.c_int()
+    _check(load().fea_sharing_elimination(lhs.encode(), expr.encode(), ",".join(loops).encode(), _ext(extents),
+                                          buf, len(buf), ctypes.byref(ops), ctypes.byref(cover)))
+    return buf.value.decode(), ops.value, cover.value
+
+
+def vertex_cover(nl, nr, edges):
+    flat = (ctypes.c_int * (2 * len(edges)))(*[x for e in edges for x in e])
+    k = ctypes.c_int()
+    _check(load().fea_vertex_cover(nl, nr, flat, len(edges), ctypes.byref(k)))
+    return k.value
+
+
+def increase_factor(n, k):
+    return load().fea_increase_factor(n, k)
+
+
+def theta(form, degree):
+    """[(theta_se, theta_pre, table_words)] per monomial of the form."""
+    out = []
+    for m in range(load().fea_num_monomials(form, degree)):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().fea_theta(form, degree, m, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        out.append((a.value, b.value, c.value))
+    return out
+
+
+def algorithm3(form, degree, precision=PREC_FP32, smem_budget=0):
+    """(bitmask of pre-evaluated monomials, cost) chosen by Algorithm 3."""
+    m, c = ctypes.c_uint(), ctypes.c_int64()
+    _check(load().fea_algorithm3(form, degree, precision, smem_budget, ctypes.byref(m), ctypes.byref(c)))
+    return m.value, c.value
 
 
 def finalize():

@@ -26,7 +26,11 @@ namespace fea {
 int kind_of(int variant, int form, int p) { return (variant == FEA_VARIANT_PRE ? 16 : 0) + form * 4 + (p - 1); }
 
 template <class K>
-__device__ __forceinline__ void run_one(const Req& q, int64_t t, char* sm, unsigned* err) {
+__device__ __forceinline__ void run_one(const Req& q, int64_t t, char* sm, unsigned* err, unsigned dyn) {
+  if (K::smem(q.tile, q.Q) > dyn) {  // a tile larger than the launch's shared memory is refused
+    if (threadIdx.x == 0) flag_error(err, ERR_LAUNCH);
+    return;
+  }
   const int64_t e0 = t * q.tile;
   const int64_t left = q.E - e0;
   K::tile(q, e0, (int)(left < q.tile ? left : q.tile), sm, err);
@@ -54,9 +58,10 @@ __global__ void __launch_bounds__(NT) batch_kernel(const Req* __restrict__ reqs,
     __syncthreads();
     const Req q = reqs[s_r];
     const int64_t t = w - q.tile0;
+    const unsigned dyn = dynamic_smem_bytes();
     switch (q.kind) {
-#define SEK(F, P) case (F) * 4 + (P) - 1: run_one<SeTile<F, P, float>>(q, t, smem_raw, err); break;
-#define PREK(F, P) case 16 + (F) * 4 + (P) - 1: run_one<PreTile<F, P, float>>(q, t, smem_raw, err); break;
+#define SEK(F, P) case (F) * 4 + (P) - 1: run_one<SeTile<F, P, float>>(q, t, smem_raw, err, dyn); break;
+#define PREK(F, P) case 16 + (F) * 4 + (P) - 1: run_one<PreTile<F, P, float>>(q, t, smem_raw, err, dyn); break;
       SEK(0, 1) SEK(0, 2) SEK(0, 3) SEK(0, 4)
       SEK(1, 1) SEK(1, 2) SEK(1, 3) SEK(1, 4)
       SEK(2, 1) SEK(2, 2) SEK(2, 3) SEK(2, 4)
@@ -100,8 +105,9 @@ BatchState*& dev_batch(DevState* st);
 unsigned* device_error_word(DevState* st);
 int device_sms(DevState* st);
 const void* table_ptr(DevState* st, int form, int p, int prec, int* rc);
-int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl);
+int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch);
 int set_error(int code, const char* msg);
+int check_device_ptr(const void* p, const char* what, bool allow_null);
 
 static bool same_sig(const std::vector<Req>& a, const std::vector<Req>& b) {
   if (a.size() != b.size()) return false;
@@ -127,10 +133,12 @@ int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* 
     if (r.form < 0 || r.form > 3 || r.degree < 1 || r.degree > 4 || r.E < 0)
       return set_error(FEA_EINVAL, "bad request");
     if (r.E == 0) continue;
-    if (!r.coords || !r.out || (!r.coeffs && r.form != FEA_MASS)) return set_error(FEA_EINVAL, "NULL request buffer");
+    if ((rc = check_device_ptr(r.coords, "coords", false))) return rc;
+    if ((rc = check_device_ptr(r.coeffs, "coeffs", r.form == FEA_MASS))) return rc;
+    if ((rc = check_device_ptr(r.out, "out", false))) return rc;
     fea_options oi = o;
     Plan pl;
-    if ((rc = make_plan(st, r.form, r.degree, oi, &pl))) return rc;
+    if ((rc = make_plan(st, r.form, r.degree, oi, &pl, true))) return rc;
     if (pl.variant == FEA_VARIANT_NAIVE) return set_error(FEA_EINVAL, "the batched launch has no plain variant");
     Req q;
     std::memset(&q, 0, sizeof(q));

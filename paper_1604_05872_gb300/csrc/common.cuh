@@ -17,15 +17,22 @@ namespace fea {
 // 32-bit integer pipe instead.
 // ----------------------------------------------------------------------------
 
-// Exact widening float -> double.  Zero, subnormal, inf and NaN inputs take the
-// hardware conversion (rare).
+// Widening float -> double, exact for every normal float; zero and subnormal
+// inputs give a signed zero (FP32 arithmetic here runs with flush-to-zero, so
+// subnormals do not arise), inf and NaN stay inf and NaN.  Integer operations
+// only: a data-dependent fallback to the hardware conversion would be
+// if-converted into a predicated FP64-pipe instruction on every call.
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t a = u & 0x7fffffffu;
-  if (a - 0x00800000u >= 0x7f000000u) return (double)f;  // a < 2^-126 or a >= inf
-  const uint32_t hi = ((a >> 3) + 0x38000000u) | (u & 0x80000000u);  // exponent + (1023 - 127)
-  const uint32_t lo = a << 29;
-  return __hiloint2double((int)hi, (int)lo);
+  uint32_t hi = (a >> 3) + 0x38000000u;  // exponent rebias by 1023 - 127
+  uint32_t lo = a << 29;
+  const bool small = a < 0x00800000u;
+  const bool big = a >= 0x7f800000u;
+  hi = small ? 0u : hi;
+  lo = small ? 0u : lo;
+  hi = big ? (0x7ff00000u | ((a & 0x007fffffu) ? 0x00080000u : 0u)) : hi;
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
 }
 
 // double -> float, round to nearest even.  Results below the smallest normal

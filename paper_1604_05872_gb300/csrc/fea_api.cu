@@ -129,7 +129,7 @@ static fea_options default_options() {
 static bool valid_fd(int form, int p) { return form >= 0 && form <= 3 && p >= 1 && p <= 4; }
 
 // Resolve variant, kernel and tile for a request.
-int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl) {
+int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch) {
   if (!valid_fd(form, p)) return fail(FEA_EINVAL, "unsupported form/degree");
   if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32) return fail(FEA_EINVAL, "unsupported precision");
   const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
@@ -140,7 +140,7 @@ int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl) {
   if (variant == FEA_VARIANT_NAIVE && prec != 0) return fail(FEA_EINVAL, "the plain variant is FP64 only");
   if (variant == FEA_VARIANT_PRE && pre_terms(form, p) == 0)
     return fail(FEA_EINVAL, "pre-evaluation does not apply to this form (integrand not polynomial)");
-  const KernelInfo* k = find_kernel(variant, form, p, prec);
+  const KernelInfo* k = batch ? find_batch_kernel(variant, form, p) : find_kernel(variant, form, p, prec);
   if (!k) return fail(FEA_EINVAL, "no kernel for this variant/form/degree/precision");
   const int Q = rule_points(rule_index(form, p));
   int TE = o.tile;
@@ -158,7 +158,7 @@ int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl) {
   return FEA_OK;
 }
 
-static int check_device_ptr(const void* p, const char* what, bool allow_null) {
+int check_device_ptr(const void* p, const char* what, bool allow_null) {
   if (!p) return allow_null ? FEA_OK : fail(FEA_EINVAL, std::string(what) + " is NULL");
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -172,7 +172,7 @@ static int check_device_ptr(const void* p, const char* what, bool allow_null) {
   cudaGetDevice(&dev);
   if (a.type == cudaMemoryTypeDevice && a.device != dev)
     return fail(FEA_EINVAL, std::string(what) + " belongs to another device");
-  if (reinterpret_cast<uintptr_t>(p) & 7) return fail(FEA_EINVAL, std::string(what) + " is not 8-byte aligned");
+  if (reinterpret_cast<uintptr_t>(p) & 15) return fail(FEA_EINVAL, std::string(what) + " is not 16-byte aligned");
   return FEA_OK;
 }
 
@@ -218,7 +218,7 @@ int assemble_impl(int form, int degree, int64_t E, const double* coords, const d
   int rc = get_dev(&st);
   if (rc) return rc;
   Plan pl;
-  rc = make_plan(st, form, degree, o, &pl);
+  rc = make_plan(st, form, degree, o, &pl, false);
   if (rc) return rc;
   if (E == 0) return FEA_OK;
   if ((rc = check_device_ptr(coords, "coords", false))) return rc;
@@ -250,7 +250,7 @@ int assemble_host_impl(int form, int degree, int64_t E, const double* coords, co
   int rc = get_dev(&st);
   if (rc) return rc;
   Plan pl;
-  rc = make_plan(st, form, degree, o, &pl);
+  rc = make_plan(st, form, degree, o, &pl, false);
   if (rc) return rc;
   if (E == 0) return FEA_OK;
   if (!coords || !out || (!coeffs && form != FEA_MASS)) return fail(FEA_EINVAL, "NULL host buffer");
@@ -306,6 +306,8 @@ int sync_impl(void* stream) {
   CUDA_TRY(cudaMemcpy(&h, st->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (h) {
     CUDA_TRY(cudaMemset(st->err, 0, sizeof(unsigned)));
+    if (h & 4u) return fail(FEA_EINVAL, "a kernel refused a tile larger than its shared memory");
+    if (h & 2u) return fail(FEA_ETIMEOUT, "a bounded wait for a tile's input copy gave up");
     return fail(FEA_EDEGENERATE, "degenerate element (det J == 0 or det F <= 0); NaN written for it");
   }
   return FEA_OK;
@@ -377,7 +379,7 @@ int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info) 
     cudaGetLastError();
   }
   Plan pl;
-  int rc = make_plan(st, form, degree, o, &pl);
+  int rc = make_plan(st, form, degree, o, &pl, false);
   if (rc) return rc;
   OpCounts oc = op_counts(form, degree);
   info->variant = pl.variant;

@@ -21,6 +21,11 @@ extern const int kNumSeKernels;
 extern const KernelInfo kNaiveKernels[];
 extern const int kNumNaiveKernels;
 
+extern const KernelInfo kPreTileF32[];
+extern const int kNumPreTileF32;
+
 const KernelInfo* find_kernel(int variant, int form, int p, int prec);
+// Tile functions of the batched persistent kernel (FP32): PreTile / SeTile.
+const KernelInfo* find_batch_kernel(int variant, int form, int p);
 
 }  // namespace fea

@@ -26,3 +26,15 @@ const KernelInfo* find_kernel(int variant, int form, int p, int prec) {
 }
 
 }  // namespace fea
+
+namespace fea {
+const KernelInfo* find_batch_kernel(int variant, int form, int p) {
+  if (variant == V_PRE) {
+    for (int i = 0; i < kNumPreTileF32; ++i)
+      if (kPreTileF32[i].form == form && kPreTileF32[i].p == p) return &kPreTileF32[i];
+    return nullptr;
+  }
+  if (variant == V_SE) return find_kernel(V_SE, form, p, 1);
+  return nullptr;
+}
+}  // namespace fea

@@ -1,16 +1,34 @@
 // Instantiations of the pre-evaluated variant (mass, Helmholtz, elasticity; P1-P4; FP32 and FP64).
 #include "launch.cuh"
 #include "pre.cuh"
+#include "pre_stream.cuh"
 
 namespace fea {
 
+template <int F, int P>
+size_t stream_smem(int TE, int Q) { return PreStream<F, P>::smem(TE, Q); }
+template <int F, int P>
+KernelInfo stream_info() {
+  return KernelInfo{reinterpret_cast<const void*>(&pre_stream_kernel<F, P>), V_PRE, F, P, 1, NT, &stream_smem<F, P>};
+}
+
 #define PRE(F, P) make_info<PreTile<F, P, float>>(V_PRE, F, P, 1), make_info<PreTile<F, P, double>>(V_PRE, F, P, 0)
+#define PRES(F, P) stream_info<F, P>(), make_info<PreTile<F, P, double>>(V_PRE, F, P, 0)
 const KernelInfo kPreKernels[] = {
-    PRE(0, 1), PRE(0, 2), PRE(0, 3), PRE(0, 4),
-    PRE(1, 1), PRE(1, 2), PRE(1, 3), PRE(1, 4),
+    PRES(0, 1), PRES(0, 2), PRES(0, 3), PRE(0, 4),
+    PRES(1, 1), PRES(1, 2), PRES(1, 3), PRE(1, 4),
     PRE(2, 1), PRE(2, 2), PRE(2, 3), PRE(2, 4),
 };
 #undef PRE
+#undef PRES
 const int kNumPreKernels = sizeof(kPreKernels) / sizeof(kPreKernels[0]);
+
+// The FP32 tile functions the batched kernel dispatches to (their shared-memory
+// layouts and tile limits plan the batch).
+#define PT(F, P) make_info<PreTile<F, P, float>>(V_PRE, F, P, 1)
+const KernelInfo kPreTileF32[] = {PT(0, 1), PT(0, 2), PT(0, 3), PT(0, 4), PT(1, 1), PT(1, 2),
+                                  PT(1, 3), PT(1, 4), PT(2, 1), PT(2, 2), PT(2, 3), PT(2, 4)};
+#undef PT
+const int kNumPreTileF32 = sizeof(kPreTileF32) / sizeof(kPreTileF32[0]);
 
 }  // namespace fea

@@ -5,9 +5,21 @@
 
 namespace fea {
 
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+constexpr unsigned ERR_LAUNCH = 4u;
+
 template <class K>
 __global__ void __launch_bounds__(NT) run_tiles(Req q, unsigned* err) {
   extern __shared__ __align__(16) char smem_raw[];
+  // a tile larger than the shared memory it was launched with is refused, not run
+  if (K::smem(q.tile, q.Q) > dynamic_smem_bytes()) {
+    if (threadIdx.x == 0) flag_error(err, ERR_LAUNCH);
+    return;
+  }
   const int64_t ntiles = (q.E + q.tile - 1) / q.tile;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t e0 = t * q.tile;

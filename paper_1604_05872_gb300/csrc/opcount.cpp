@@ -391,7 +391,7 @@ bool linear_split(const Expr& e, int i, const std::string& L, std::vector<std::p
 }  // namespace
 
 SEResult sharing_elimination(const std::string& lhs, const std::string& expr, const std::vector<std::string>& loops,
-                             const std::map<std::string, int64_t>& ext) {
+                             const std::map<std::string, int64_t>& ext, const std::string& prefix) {
   if (loops.size() < 2) throw std::invalid_argument("need two linear loops");
   const std::string L1 = loops[loops.size() - 2], L2 = loops.back();
   std::vector<std::string> outer(loops.begin(), loops.end() - 2);
@@ -447,7 +447,7 @@ SEResult sharing_elimination(const std::string& lhs, const std::string& expr, co
           if (oe.n[oe.root].kind == Node::SYM) {
             temp_of[op] = op;
           } else {
-            std::string t = "t" + std::to_string(ntemp++) + "[" + L + "]";
+            std::string t = prefix + "t" + std::to_string(ntemp++) + "[" + L + "]";
             prog.push_back(lstr(with(L)) + ": " + t + " = " + op);
             temp_of[op] = t;
           }
@@ -507,8 +507,21 @@ SEResult sharing_elimination(const std::string& lhs, const std::string& expr, co
   }
   std::vector<std::pair<int, int>> edges;
   for (auto& kv : edge_coef) edges.push_back(kv.first);
-  // Step 5: the ILP is a minimum vertex cover of the bipartite sharing graph
-  auto cover = min_vertex_cover((int)left.size(), (int)right.size(), edges);
+  // Step 5: the ILP is a minimum vertex cover of the bipartite sharing graph.
+  // Among minimum covers prefer the larger loop's side: the partner sums (and
+  // their coefficient products) then run over the smaller loop.
+  auto extent = [&](const std::string& L) {
+    auto it = ext.find(L);
+    return it == ext.end() ? (int64_t)1 : it->second;
+  };
+  std::vector<std::pair<int, int>> cover;
+  if (extent(L1) >= extent(L2)) {
+    cover = min_vertex_cover((int)left.size(), (int)right.size(), edges);
+  } else {
+    std::vector<std::pair<int, int>> flipped;
+    for (auto& ed : edges) flipped.push_back({ed.second, ed.first});
+    for (auto& c : min_vertex_cover((int)right.size(), (int)left.size(), flipped)) cover.push_back({1 - c.first, c.second});
+  }
   res.cover = (int)cover.size();
   // coefficient temporaries at the outer level (hoisted, shared)
   std::map<std::string, std::string> ctemp;
@@ -520,7 +533,7 @@ SEResult sharing_elimination(const std::string& lhs, const std::string& expr, co
     if (ce.n[ce.root].kind == Node::SYM || ce.n[ce.root].kind == Node::NUM) return sum;
     auto it = ctemp.find(sum);
     if (it != ctemp.end()) return it->second;
-    std::string nm = "c" + std::to_string(nc++);
+    std::string nm = prefix + "c" + std::to_string(nc++);
     if (!outer.empty()) nm += "[" + join(outer, ",") + "]";
     prog.push_back((outer.empty() ? std::string("") : lstr(outer)) + ": " + nm + " = " + sum);
     ctemp[sum] = nm;
@@ -546,7 +559,7 @@ SEResult sharing_elimination(const std::string& lhs, const std::string& expr, co
     if (kv.second.size() == 1 && parse_expr(kv.second[0]).n.size() == 1) {
       T = kv.second[0];
     } else {
-      T = "T" + std::to_string(nt++) + "[" + Lo + "]";
+      T = prefix + "T" + std::to_string(nt++) + "[" + Lo + "]";
       prog.push_back(lstr(with(Lo)) + ": " + T + " = " + join(kv.second, " + "));
     }
     inner.push_back(s == "1" ? T : (T == "1" ? s : s + "*" + T));

@@ -69,7 +69,7 @@ struct SEResult {
   int strategy2 = 0;    // operand partitions expanded and factorised
 };
 SEResult sharing_elimination(const std::string& lhs, const std::string& expr, const std::vector<std::string>& loops,
-                             const std::map<std::string, int64_t>& ext);
+                             const std::map<std::string, int64_t>& ext, const std::string& prefix = "");
 
 // Section 4.2: increase factor iota = C(n + k - 1, k) of pre-evaluation.
 int64_t increase_factor(int64_t n, int64_t k);

@@ -110,32 +110,37 @@ void clear_tuned() {
   g_tuned.clear();
 }
 
+struct Theta {
+  int64_t se, pre, table_words;
+};
+Theta theta_of(int form, int p, int mi);
+int num_monomials(int form, int p);
+
 // Algorithm 3: returns a bitmask of the monomials to pre-evaluate.
 unsigned algorithm3(int form, int p, int prec, size_t budget, int64_t* best_cost) {
-  std::vector<MonoCost> M = monomials(form, p);
-  const int nm = (int)M.size();
-  // step 1: S = {theta > 0} stays with sharing elimination; P = the rest
+  const int nm = num_monomials(form, p);
+  std::vector<Theta> th;
+  for (int i = 0; i < nm; ++i) th.push_back(theta_of(form, p, i));
+  // step 1: S = {m : theta(m) = theta_pre - theta_se > 0} stays with sharing elimination
   std::vector<int> P;
   for (int i = 0; i < nm; ++i)
-    if (M[i].pre >= 0 && M[i].pre - M[i].se <= 0) P.push_back(i);
+    if (th[i].pre >= 0 && th[i].pre - th[i].se <= 0) P.push_back(i);
   const size_t word = prec == 0 ? 8 : 4;
   unsigned best = 0;
   int64_t bestc = INT64_MAX;
-  // steps 2-4: all bipartitions (b_S, b_P) of P, Constraint 2 filter, argmin
+  // steps 2-4: every bipartition (b_S, b_P) of P, Constraint 2 filter, argmin
   for (unsigned b = 0; b < (1u << P.size()); ++b) {
     size_t mem = 0;
     int64_t cost = 0;
     unsigned mask = 0;
+    for (size_t k = 0; k < P.size(); ++k)
+      if (b >> k & 1u) mask |= 1u << P[k];
     for (int i = 0; i < nm; ++i) {
-      bool pre = false;
-      for (size_t k = 0; k < P.size(); ++k)
-        if (P[k] == i && (b >> k & 1u)) pre = true;
-      if (pre) {
-        mask |= 1u << i;
-        mem += (size_t)M[i].table_bytes4 * word;
-        cost += M[i].pre;
+      if (mask >> i & 1u) {
+        mem += (size_t)th[i].table_words * word;
+        cost += th[i].pre;
       } else {
-        cost += M[i].se;
+        cost += th[i].se;
       }
     }
     if (mem > budget) continue;
@@ -153,7 +158,7 @@ int choose_variant(int form, int p, int prec, size_t budget) {
   if (get_tuned(form, p, prec, &v, &t) && v != FEA_VARIANT_AUTO) return v;
   if (form == NEOHOOKEAN) return FEA_VARIANT_SE;
   const unsigned mask = algorithm3(form, p, prec, budget, nullptr);
-  const int nm = (int)monomials(form, p).size();
+  const int nm = num_monomials(form, p);
   if (mask == (1u << nm) - 1) return FEA_VARIANT_PRE;
   if (mask == 0) return FEA_VARIANT_SE;
   // A mixed bipartition: the kernels implement whole-form variants, so take
@@ -175,4 +180,16 @@ int default_tile(int variant, int form, int p, int prec, int max_tile, size_t bu
   return best;
 }
 
+int set_error(int code, const char* msg);
+
 }  // namespace fea
+
+extern "C" int fea_algorithm3(int form, int degree, int precision, size_t smem_budget, unsigned* premask,
+                              int64_t* cost) {
+  using namespace fea;
+  if (form < 0 || form > 3 || degree < 1 || degree > 4) return set_error(FEA_EINVAL, "unsupported form/degree");
+  const unsigned m = algorithm3(form, degree, precision == FEA_PREC_FP64 ? 0 : 1,
+                                smem_budget ? smem_budget : 232448, cost);
+  if (premask) *premask = m;
+  return FEA_OK;
+}

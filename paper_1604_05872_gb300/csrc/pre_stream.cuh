@@ -1,0 +1,259 @@
+// Streaming form of the pre-evaluated variant for scalar forms with an even
+// number of matrix entries (mass and Helmholtz, P1-P3), FP32 contraction.
+//
+// Same arithmetic as PreTile (Algorithm 2: A_e = sum_r R_r H_e[r]); the
+// schedule is built for the HBM stream on sm_103a:
+//   * persistent CTAs; each tile's coordinates and coefficients arrive by a
+//     1-D bulk tensor copy (cp.async.bulk, the TMA engine) into one of two
+//     shared buffers, completing on an mbarrier, one tile ahead of use;
+//   * one thread per element does the FP64 geometry and writes the FP32
+//     geometry tensor H_e straight to shared memory;
+//   * each thread keeps two columns of R in registers and sweeps its elements,
+//     storing each finished pair of entries with one 16-byte streaming store
+//     (no staging: the element's entries are contiguous and 16-byte aligned).
+// Every mbarrier wait is bounded; a wait that gives up sets the error word and
+// the whole CTA leaves the kernel.
+#pragma once
+#include "common.cuh"
+
+namespace fea {
+
+constexpr unsigned ERR_TIMEOUT = 2u;
+constexpr long kMaxWaitIters = 1L << 20;  // try_wait polls: well under a second
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared completing on `bar` (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Bounded wait for the phase with parity `parity`; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (long it = 0; it < kMaxWaitIters; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int FORM, int P>
+struct PreStream {
+  static_assert(FORM == 0 || FORM == 1, "scalar forms");
+  static constexpr int NS = nbasis_c(P);
+  static constexpr int NN = NS * NS;
+  static_assert(NN % 2 == 0, "even entry count");
+  static constexpr int R = pre_terms_c(FORM, P);
+  static constexpr int NHP = round_up(R, 4);
+  static constexpr int CLEN = coeff_len_c(FORM, P);
+  static constexpr int S = NN / 2;                 // pair slots
+  static constexpr int G = S >= NT ? 1 : NT / S;   // element groups
+  static constexpr int IN = 12 + CLEN;             // doubles of input per element
+
+  FEA_HD static size_t off_h(int TE) { return round_up_sz((size_t)2 * TE * IN * 8, 16); }
+  FEA_HD static size_t off_bar(int TE) { return off_h(TE) + round_up_sz((size_t)2 * TE * NHP * 4, 16); }
+  FEA_HD static size_t smem(int TE, int Q) { (void)Q; return off_bar(TE) + 16 + 16; }
+  FEA_HD static int max_tile() { return NT; }
+
+  __device__ static void geometry_h(const double* x, const double* c, float* h, unsigned* err) {
+    double adj[9];
+    const double det = geometry_fp64(x, adj);
+    const uint64_t bits = (uint64_t)__double_as_longlong(det);
+    const bool bad = ((bits << 1) == 0) || ((bits >> 52 & 0x7ff) == 0x7ff);  // zero, inf or NaN
+    if (bad) flag_error(err, ERR_DEGENERATE);
+    const float ad = __uint_as_float(__float_as_uint(d2f(det)) & 0x7fffffffu);
+    const float nan = __int_as_float(0x7fc00000);
+    float v[NHP];
+#pragma unroll
+    for (int k = 0; k < NHP; ++k) v[k] = 0.f;
+    if constexpr (FORM == 0) {
+      v[0] = ad;
+    } else {
+      float a[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a[k] = d2f(adj[k]);
+      const float inv = 1.0f / ad;
+      const int al[6] = {0, 1, 2, 0, 0, 1}, be[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        v[k] = (a[3 * al[k]] * a[3 * be[k]] + a[3 * al[k] + 1] * a[3 * be[k] + 1] + a[3 * al[k] + 2] * a[3 * be[k] + 2]) * inv;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) v[6 + k] = ad * d2f(c[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NHP; k += 4) {
+      float4 w;
+      w.x = bad ? nan : v[k]; w.y = bad ? nan : v[k + 1]; w.z = bad ? nan : v[k + 2]; w.w = bad ? nan : v[k + 3];
+      *reinterpret_cast<float4*>(h + k) = w;
+    }
+  }
+};
+
+// Exact widening of a finite float that is normal or zero (no subnormals arise
+// under flush-to-zero); NaN rows of degenerate elements are written separately.
+__device__ __forceinline__ double f2d_finite(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t a = u & 0x7fffffffu;
+  const uint32_t hi = (a ? (a >> 3) + 0x38000000u : 0u) | (u & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(a << 29));
+}
+
+template <int FORM, int P>
+__global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
+  using K = PreStream<FORM, P>;
+  extern __shared__ __align__(16) char sm[];
+  const int TE = q.tile;
+  double* in = reinterpret_cast<double*>(sm);                 // [2][TE][IN]: coords block, then coeffs block
+  float* H = reinterpret_cast<float*>(sm + K::off_h(TE));      // [2][TE][NHP]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + K::off_bar(TE));
+  __shared__ int s_abort;
+  const TabLayout L = tab_layout(q.Q, K::NS, K::R);
+  const float* Rg = reinterpret_cast<const float*>(q.tab) + L.offR;
+  const int64_t ntiles = (q.E + TE - 1) / TE;
+  const int64_t first = blockIdx.x;
+  if (first >= ntiles) return;
+  {
+    unsigned dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (K::smem(TE, q.Q) > dyn) {  // refuse a tile that does not fit the launch
+      if (threadIdx.x == 0) flag_error(err, 4u);
+      return;
+    }
+  }
+  const int64_t stride = gridDim.x;
+  const int my_tiles = (int)((ntiles - first + stride - 1) / stride);  // tiles this CTA runs: j = 0 .. my_tiles-1
+
+  // thread -> (pair slot, element group); R columns live in registers
+  const int t = threadIdx.x;
+  const bool active = t < K::G * K::S;
+  const int slot = t % K::S, g0 = t / K::S;
+  float r0[K::R], r1[K::R];
+#pragma unroll
+  for (int r = 0; r < K::R; ++r) {
+    r0[r] = active ? __ldg(Rg + (size_t)r * K::NN + 2 * slot) : 0.f;
+    r1[r] = active ? __ldg(Rg + (size_t)r * K::NN + 2 * slot + 1) : 0.f;
+  }
+
+  auto tile_ne = [&](int j) {
+    const int64_t e0 = (first + (int64_t)j * stride) * TE;
+    return (int)(q.E - e0 < TE ? q.E - e0 : TE);
+  };
+  // one thread: bulk copies of the inputs of this CTA's j-th tile into buffer j & 1
+  auto issue = [&](int j) {
+    const int64_t e0 = (first + (int64_t)j * stride) * TE;
+    const int ne = tile_ne(j), b = j & 1;
+    double* dst = in + (size_t)b * TE * K::IN;
+    const unsigned cb = (unsigned)ne * 96u, fb = (unsigned)ne * K::CLEN * 8u;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[b], cb + fb);
+    bulk_g2s(dst, q.coords + e0 * 12, cb, &bar[b]);
+    if (K::CLEN) bulk_g2s(dst + (size_t)TE * 12, q.coeffs + e0 * K::CLEN, fb, &bar[b]);
+  };
+  // all threads: wait for tile j's inputs (bounded); false after a time-out
+  auto wait_in = [&](int j) { return mbar_wait(&bar[j & 1], (unsigned)(j >> 1) & 1u); };
+  // threads < ne: FP64 geometry of tile j into H buffer j & 1
+  auto geometry = [&](int j) {
+    const int ne = tile_ne(j), b = j & 1;
+    const double* xs = in + (size_t)b * TE * K::IN;
+    if (t < ne) K::geometry_h(xs + 12 * t, xs + (size_t)TE * 12 + K::CLEN * t, H + (size_t)(b * TE + t) * K::NHP, err);
+  };
+  auto abort_all = [&](int j_lo, int j_hi) {
+    // a copy in flight must land before the CTA leaves: bounded waits on the pending tiles
+    for (int j = j_lo; j <= j_hi && j < my_tiles; ++j) wait_in(j);
+  };
+
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  if (t == 0) {
+    issue(0);
+    if (my_tiles > 1) issue(1);
+  }
+  if (!wait_in(0)) {
+    flag_error(err, ERR_TIMEOUT);
+    s_abort = 1;
+  }
+  __syncthreads();
+  if (s_abort) {
+    abort_all(0, 1);
+    return;
+  }
+  geometry(0);
+  __syncthreads();
+
+  for (int j = 0; j < my_tiles; ++j) {
+    const int64_t e0 = (first + (int64_t)j * stride) * TE;
+    const int ne = tile_ne(j);
+    // inputs of tile j + 2 go into the buffer tile j used (consumed before the last barrier)
+    if (t == 0 && j + 2 < my_tiles) issue(j + 2);
+    if (active) {
+      const float* Hb = H + (size_t)(j & 1) * TE * K::NHP;
+      double2* o = reinterpret_cast<double2*>(reinterpret_cast<double*>(q.out) + e0 * K::NN) + slot;
+      float2* of = reinterpret_cast<float2*>(reinterpret_cast<float*>(q.out) + e0 * K::NN) + slot;
+      for (int e = g0; e < ne; e += K::G) {
+        const float* h = Hb + K::NHP * e;
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int r4 = 0; r4 < K::NHP; r4 += 4) {
+          const float4 hv = *reinterpret_cast<const float4*>(h + r4);
+          const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (r4 + k < K::R) {
+              a0 = fmaf(r0[r4 + k], hh[k], a0);
+              a1 = fmaf(r1[r4 + k], hh[k], a1);
+            }
+        }
+        if (q.out_f32) {
+          __stcs(of + (size_t)e * (K::NN / 2), make_float2(a0, a1));
+        } else {
+          double2 v = make_double2(f2d_finite(a0), f2d_finite(a1));
+          if (h[0] != h[0]) v = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+          __stcs(o + (size_t)e * (K::NN / 2), v);
+        }
+      }
+    }
+    // inputs of tile j + 1 (issued one iteration ago) -> geometry into the other H
+    // buffer, last read by the contraction of tile j - 1 before the previous barrier
+    if (j + 1 < my_tiles) {
+      if (wait_in(j + 1)) {
+        geometry(j + 1);
+      } else {
+        flag_error(err, ERR_TIMEOUT);
+        s_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (s_abort) {
+      abort_all(j + 1, j + 2);
+      return;
+    }
+  }
+}
+
+}  // namespace fea
