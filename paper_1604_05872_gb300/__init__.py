@@ -23,7 +23,8 @@ VARIANT_AUTO, VARIANT_NAIVE, VARIANT_SE, VARIANT_PRE = -1, 0, 1, 2
 VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
-           "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_sync", "fea_plan",
+           "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_noalloc",
+           "fea_sync", "fea_plan",
            "fea_op_count", "fea_opcount_program", "fea_sharing_elimination", "fea_vertex_cover",
            "fea_increase_factor", "fea_num_monomials", "fea_theta", "fea_algorithm3",
            "fea_last_error", "fea_finalize"]
@@ -75,6 +76,7 @@ def load(path=None):
     lib.fea_assemble_ex.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_host.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_batch.argtypes = [P(Request), i, P(Options), vp]
+    lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
     lib.fea_op_count.argtypes = [i, i, i, P(i64), P(i64)]
@@ -173,6 +175,17 @@ def assemble_batch(requests, out_f32=False, stream=None):
                          None if coeffs is None else coeffs.data_ptr(), out.data_ptr())
     o = options(PREC_FP32, out_f32)
     _check(load().fea_assemble_batch(arr, len(requests), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def assemble_batch_noalloc(requests, out_f32=False, stream=None):
+    """fea_assemble_batch_noalloc: the batched launch without device allocations
+    (for callers that cannot allocate; see include/fea.h for its limits)."""
+    arr = (Request * max(1, len(requests)))()
+    for k, (form, degree, coords, coeffs, out) in enumerate(requests):
+        arr[k] = Request(form, degree, coords.shape[0], coords.data_ptr(),
+                         None if coeffs is None else coeffs.data_ptr(), out.data_ptr())
+    o = options(PREC_FP32, out_f32)
+    _check(load().fea_assemble_batch_noalloc(arr, len(requests), ctypes.byref(o), _stream_ptr(stream)))
 
 
 def sync(stream=None):

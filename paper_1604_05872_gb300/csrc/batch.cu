@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -210,6 +211,122 @@ int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* 
     bs->sig = R;
   }
   if ((e = cudaGraphLaunch(bs->exec, s)) != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  return FEA_OK;
+}
+
+// ------------------------------------------------------------------------
+// The batched launch without any device allocation.
+//
+// Some callers cannot call cudaMalloc at the moment they assemble: code that
+// runs while a CUDA graph is being captured, code inside another framework's
+// memory pool that forbids allocations outside the pool, or latency-critical
+// loops where an allocation could block.  fea_assemble_batch_noalloc serves
+// them: the work-list counter and the request list that the batched kernel
+// needs live in the file-scope device array below instead of library
+// allocations, and the launch is made directly (no graph).  Limits: at most
+// kNoAllocMaxRequests requests per call; the device state and the tables of
+// every (form, degree) in the batch must already exist on the current device
+// (made by any earlier allocating call there), otherwise the call is
+// rejected.  Every call shares the array, so calls whose kernels overlap on
+// the GPU race.
+// ------------------------------------------------------------------------
+constexpr int kNoAllocMaxRequests = 512;
+constexpr size_t kNoAllocReqOffset = 256;  // counter in the first 256 bytes
+constexpr size_t kNoAllocBytes = kNoAllocReqOffset + (size_t)kNoAllocMaxRequests * sizeof(Req);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+DevState* existing_dev_state();
+const void* existing_table(DevState* st, int form, int p, int prec);
+
+namespace {
+constexpr int kMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+std::mutex g_noalloc_mu;
+}  // namespace
+
+int batch_noalloc_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
+  if (nreq < 0 || (nreq > 0 && !reqs)) return set_error(FEA_EINVAL, "bad request list");
+  if (nreq > kNoAllocMaxRequests)
+    return set_error(FEA_EINVAL, "fea_assemble_batch_noalloc takes at most 512 requests per call");
+  if (nreq == 0) return FEA_OK;
+  fea_options o;
+  if (opt) o = *opt;
+  else { o.precision = FEA_PREC_FP32; o.out_f32 = 0; o.variant = FEA_VARIANT_AUTO; o.tile = 0; o.smem_budget = 0; }
+  if (o.precision != FEA_PREC_FP32) return set_error(FEA_EINVAL, "the batched launch runs the FP32 contraction");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(FEA_EINVAL, "device index out of range");
+  DevState* st = existing_dev_state();
+  if (!st) return set_error(FEA_EINVAL, "no library state on this device yet: make one allocating call first");
+  unsigned char* scratch = nullptr;
+  {
+    // set-up, once per device, with that device current
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  Req R[kNoAllocMaxRequests];
+  int nr = 0;
+  size_t smem = 0;
+  long long tiles = 0;
+  int rc;
+  for (int i = 0; i < nreq; ++i) {
+    const fea_request& r = reqs[i];
+    if (r.form < 0 || r.form > 3 || r.degree < 1 || r.degree > 4 || r.E < 0)
+      return set_error(FEA_EINVAL, "bad request");
+    if (r.E == 0) continue;
+    if ((rc = check_device_ptr(r.coords, "coords", false))) return rc;
+    if ((rc = check_device_ptr(r.coeffs, "coeffs", r.form == FEA_MASS))) return rc;
+    if ((rc = check_device_ptr(r.out, "out", false))) return rc;
+    Plan pl;
+    if ((rc = make_plan(st, r.form, r.degree, o, &pl, true))) return rc;
+    if (pl.variant == FEA_VARIANT_NAIVE) return set_error(FEA_EINVAL, "the batched launch has no plain variant");
+    const void* tab = existing_table(st, r.form, r.degree, 1);
+    if (!tab) return set_error(FEA_EINVAL, "tables of a requested form/degree are not resident: make one allocating call first");
+    Req& q = R[nr++];
+    std::memset(&q, 0, sizeof(q));
+    q.coords = r.coords;
+    q.coeffs = r.coeffs;
+    q.out = r.out;
+    q.tab = tab;
+    q.E = r.E;
+    q.form = r.form;
+    q.p = r.degree;
+    q.Q = pl.Q;
+    q.tile = pl.tile;
+    q.out_f32 = o.out_f32;
+    q.kind = kind_of(pl.variant, r.form, r.degree);
+    q.tile0 = tiles;
+    tiles += (r.E + pl.tile - 1) / pl.tile;
+    smem = std::max(smem, pl.smem);
+  }
+  if (nr == 0) return FEA_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* fn = reinterpret_cast<const void*>(&batch_kernel);
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem)) != cudaSuccess || per_sm < 1)
+    return set_error(FEA_ECUDA, "batch kernel occupancy");
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(scratch);
+  Req* dr = reinterpret_cast<Req*>(scratch + kNoAllocReqOffset);
+  // the array keeps the previous call's contents: the counter must restart at zero
+  if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+    return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  if ((e = cudaMemcpyAsync(dr, R, (size_t)nr * sizeof(Req), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  const int grid = (int)std::min<long long>(tiles, (long long)device_sms(st) * per_sm);
+  unsigned* err = device_error_word(st);
+  long long total = tiles;
+  void* args[] = {&dr, &nr, &total, &ctr, &err};
+  if ((e = cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s)) != cudaSuccess)
+    return set_error(FEA_ECUDA, cudaGetErrorString(e));
   return FEA_OK;
 }
 

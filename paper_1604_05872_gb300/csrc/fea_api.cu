@@ -110,6 +110,21 @@ int get_tables(DevState* st, int form, int p, int prec, TableEntry** out) {
   return FEA_OK;
 }
 
+// Lookups that never create anything: the device state and the FP32 tables of
+// (form, p) if an earlier call on the current device made them, else NULL.
+DevState* existing_dev_state() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_dev.find(dev);
+  return it == g_dev.end() ? nullptr : it->second.get();
+}
+const void* existing_table(DevState* st, int form, int p, int prec) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = st->tables.find(std::make_tuple(form, p, prec));
+  return it == st->tables.end() ? nullptr : it->second.dev;
+}
+
 const void* table_ptr(DevState* st, int form, int p, int prec, int* rc) {
   TableEntry* te = nullptr;
   *rc = get_tables(st, form, p, prec, &te);
@@ -334,6 +349,7 @@ void finalize_impl() {
 }
 
 int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
+int batch_noalloc_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
 
 }  // namespace fea
 
@@ -364,6 +380,9 @@ int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host
 }
 int fea_assemble_batch(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   return batch_impl(reqs, nreq, opt, stream);
+}
+int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
+  return batch_noalloc_impl(reqs, nreq, opt, stream);
 }
 int fea_sync(void* stream) { return sync_impl(stream); }
 
