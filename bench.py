@@ -166,20 +166,20 @@ def make_inputs(E, seed_offset=0):
     return coords, f
 
 
-def cpu_baseline(coords, f, budget_s=15.0):
+def cpu_baseline(form, p, coords, coeffs, budget_s=15.0):
     """FP64 oracle on a bounded sample of the workload (host cores, OpenMP over elements)."""
     import oracle
     threads = max(1, os.cpu_count() or 1)
-    n = 2000
+    n = 200
     t0 = time.perf_counter()
-    oracle.assemble(1, 2, coords[:n], f[:n], nthreads=threads)
+    oracle.assemble(form, p, coords[:n], None if coeffs is None else coeffs[:n], nthreads=threads)
     dt = time.perf_counter() - t0
-    n2 = int(min(len(coords), max(n, n * budget_s / max(dt, 1e-3) * 0.8)))
+    n2 = int(min(len(coords), max(n, n * budget_s / max(dt, 1e-4) * 0.8)))
     t0 = time.perf_counter()
-    oracle.assemble(1, 2, coords[:n2], f[:n2], nthreads=threads)
+    oracle.assemble(form, p, coords[:n2], None if coeffs is None else coeffs[:n2], nthreads=threads)
     dt = time.perf_counter() - t0
     return {"value": n2 / dt, "unit": METRIC, "cores": threads, "kind": "oracle",
-            "sample": "first %d of the 1M Helmholtz P2 elements, FP64 quadrature-mode loop nest, %.1f s" % (n2, dt)}
+            "sample": "first %d elements of the workload, FP64 quadrature-mode loop nest, %.1f s" % (n2, dt)}
 
 
 def run_reference(args, rank, world):
@@ -208,14 +208,34 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+WORKLOADS = {
+    # name: (form, degree, elements, anisotropic)
+    "helmholtz_p2_1M": (1, 2, 1_000_000, False),
+    "mass_p1_10k": (0, 1, 10_000, False),
+    "elasticity_p3_200k": (2, 3, 200_000, True),
+    "neohookean_p2_500k": (3, 2, 500_000, False),
+}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flops x max clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 lanes per clock x 2 flops x max clock
+
+
+def fp64_ops_per_element(form, p, variant, Q):
+    """FP64 operations per element of the flop-reduced kernels: 30 for the
+    geometry (J, adjugate, det), plus about 70 per point for the Neo-Hookean
+    det F, F^-1 and ln det F."""
+    return 30 + (70 * Q if form == 3 else 0)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--elements", type=int, default=WORKLOAD["elements"])
+    ap.add_argument("--workload", default="helmholtz_p2_1M", choices=sorted(WORKLOADS) + ["stream_64req_2M"])
+    ap.add_argument("--elements", type=int, default=0, help="override the element count")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--tuning", default="", help="tuning JSON (records + MLP) for the stream workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -233,95 +253,196 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fea.load()
-    E = args.elements
-    coords, f = make_inputs(E, seed_offset=rank)  # each rank its own shard (weak scaling)
-    from paper_1604_05872_gb300 import inputs
-    c = torch.from_numpy(coords).cuda()
-    fc = torch.from_numpy(inputs.coeff_array(1, 2, f)).cuda()
-    out = fea.empty_out(1, 2, E)
-    stream = torch.cuda.current_stream()
-    pl = fea.plan(1, 2)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    if args.workload == "stream_64req_2M":
+        line = run_stream(args, fea, torch, barrier, max_over_ranks, world, local)
+    else:
+        line = run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
+    from paper_1604_05872_gb300 import inputs
+    form, p, E0, aniso = WORKLOADS[args.workload]
+    E = args.elements or E0
+    coords, coeffs = inputs.workload(form, p, E, seed=inputs.SEED + rank, anisotropic=aniso)  # own shard per rank
+    c = torch.from_numpy(coords).cuda()
+    fc = None if form == 0 else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
+    out = fea.empty_out(form, p, E)
+    n = out.shape[1]
+    stream = torch.cuda.current_stream()
+    pl = fea.plan(form, p)
+
     for _ in range(args.warmup):
-        fea.assemble(1, 2, c, fc, out=out)
+        fea.assemble(form, p, c, fc, out=out)
     fea.sync()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            fea.assemble(1, 2, c, fc, out=out)
+            fea.assemble(form, p, c, fc, out=out)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     fea.sync()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms)
     value = E * world / (ms_max * 1e-3)
 
-    # plain FP64 comparator on the same workload
-    for _ in range(1):
-        fea.assemble(1, 2, c, fc, out=out, precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
+    # plain FP64 comparator on the same workload (a bounded prefix of it for the slowest forms)
+    En = int(min(E, max(1000, 0.5e12 / pl["flops_naive"])))
+    fea.assemble(form, p, c[:En], fc, out=out[:En], precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
     barrier()
     nsteps = 2
     ev0.record(stream)
     for _ in range(nsteps):
-        fea.assemble(1, 2, c, fc, out=out, precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
+        fea.assemble(form, p, c[:En], fc, out=out[:En], precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
     ev1.record(stream)
     barrier()
     ms_naive = ev0.elapsed_time(ev1) / nsteps
     fea.sync()
+    naive_rate = En / (ms_naive * 1e-3)
 
     # end to end through the host-buffer C ABI call (copies inside the timed region)
     hc = torch.from_numpy(coords).pin_memory()
-    hf = fc.cpu().pin_memory()
-    ho = torch.empty((E, 10, 10), dtype=torch.float64).pin_memory()
+    hf = None if fc is None else fc.cpu().pin_memory()
+    ho = torch.empty((E, n, n), dtype=torch.float64).pin_memory()
     for _ in range(2):
-        fea.assemble_host(1, 2, hc, hf, ho)
+        fea.assemble_host(form, p, hc, hf, ho)
     barrier()
     e2e_steps = max(3, args.steps // 4)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fea.assemble_host(1, 2, hc, hf, ho)
+        fea.assemble_host(form, p, hc, hf, ho)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3)
 
     hbm, peak_kind = peaks()
     alg_bytes = E * pl["bytes"]
-    achieved = alg_bytes / (ms * 1e-3) / 1e9
-    traffic = profiled_traffic()
-    clocks = clk.summary()
+    flops = E * pl["flops_run"]
+    f64 = E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"])
+    t_hbm = alg_bytes / (hbm * 1e9)
+    t_f32 = flops / (FP32_PEAK_TFLOPS * 1e12)
+    t_f64 = f64 / (FP64_PEAK_TFLOPS * 1e12)
+    if t_hbm >= max(t_f32, t_f64):
+        roof = {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_kind": peak_kind}
+    elif t_f32 >= t_f64:
+        roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_kind": "derived: FP32 lanes x clock"}
+    else:
+        roof = {"bound": "alu", "achieved": f64 / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (FP64)", "peak_kind": "derived: FP64 lanes x clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = profiled_traffic() if args.workload == "helmholtz_p2_1M" and E == E0 else None
+    roof["alg_bytes_per_launch"] = alg_bytes
+    roof["bound_times_ms"] = {"hbm": t_hbm * 1e3, "fp32": t_f32 * 1e3, "fp64": t_f64 * 1e3}
+    cfg = {"workload": args.workload, "form": ["mass", "helmholtz", "elasticity", "neohookean"][form],
+           "degree": p, "elements": E, "quad_points": pl["quad_points"], "local_matrix": "%dx%d f64" % (n, n),
+           "variant": fea.VARIANT_NAMES[pl["variant"]], "tile": pl["tile"], "geometry": "f64",
+           "contraction": "f32", "parallelism": "dp%d (element shards)" % world,
+           "l2": "inputs+outputs %.0f MB per step%s" % (alg_bytes / 1e6, " > 129 MB L2; no flush"
+                                                         if alg_bytes > 129e6 else " (fits L2: launch-latency bound)")}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, variant=fea.VARIANT_NAMES[pl["variant"]], tile=pl["tile"],
-                       geometry="f64", contraction="f32", parallelism="dp%d (element shards)" % world,
-                       l2="inputs+outputs %.0f MB per step > 129 MB L2; no flush" % (alg_bytes / 1e6)),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": alg_bytes},
-        "comparator": {"kernel": "plain FP64 quadrature nest", "value": E / (ms_naive * 1e-3), "unit": METRIC,
-                       "ms_per_step": ms_naive, "speedup": ms_naive / ms},
-        "e2e": {"value": E * world / (e2e_ms * 1e-3), "unit": METRIC, "h2d_bytes_per_step": E * (96 + 80),
-                "d2h_bytes_per_step": E * 800, "ms_per_step": e2e_ms},
-        "gpu_launches": args.steps,
-        "clocks": clocks,
-        "gflops": E * pl["flops_run"] / (ms * 1e-3) / 1e9,
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
+        "comparator": {"kernel": "plain FP64 quadrature nest", "value": naive_rate, "unit": METRIC,
+                       "elements": En, "ms_per_step": ms_naive, "speedup": value / world / naive_rate},
+        "e2e": {"value": E * world / (e2e_ms * 1e-3), "unit": METRIC,
+                "h2d_bytes_per_step": E * (96 + 8 * fea.coeff_len(form, p)), "d2h_bytes_per_step": E * n * n * 8,
+                "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps, "clocks": clk.summary(), "gflops": flops / (ms * 1e-3) / 1e9,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(coords, f)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+        line["cpu_baseline"] = cpu_baseline(form, p, coords, coeffs)
+    return line
+
+
+def run_stream(args, fea, torch, barrier, max_over_ranks, world, local):
+    """64 uneven requests (4 forms x P1-P4, 2M elements) in one persistent,
+    graph-captured launch; flop-count choices, then (with --tuning) the MLP's."""
+    from paper_1604_05872_gb300 import inputs
+    reqs = inputs.stream_requests()
+    built, total, alg_bytes, t_bound = [], 0, 0, 0.0
+    hbm, peak_kind = peaks()
+    for k, (form, p, E) in enumerate(reqs):
+        coords, coeffs = inputs.workload(form, p, E, seed=inputs.SEED + 100 + k, anisotropic=(form == 2))
+        c = torch.from_numpy(coords).cuda()
+        f = None if form == 0 else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
+        built.append((form, p, c, f, fea.empty_out(form, p, E)))
+        total += E
+
+    def bound_time():
+        tb, byt = 0.0, 0
+        for form, p, c, f, o in built:
+            pl = fea.plan(form, p)
+            E = c.shape[0]
+            b = E * pl["bytes"]
+            byt += b
+            tb += max(b / (hbm * 1e9), E * pl["flops_run"] / (FP32_PEAK_TFLOPS * 1e12),
+                      E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]) / (FP64_PEAK_TFLOPS * 1e12))
+        return tb, byt
+
+    def timed(steps):
+        for _ in range(args.warmup):
+            fea.assemble_batch(built)
+        fea.sync()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            fea.assemble_batch(built)
+        ev1.record()
+        barrier()
+        fea.sync()
+        return ev0.elapsed_time(ev1) / steps
+
+    fea.tune_clear()
+    t_bound, alg_bytes = bound_time()
+    with ClockSampler(local) as clk:
+        ms_flop = timed(args.steps)
+    result = {"flop_choice_ms": ms_flop}
+    ms = ms_flop
+    choice = "flop-count (Algorithm 3, default tiles)"
+    if args.tuning and os.path.exists(args.tuning):
+        from paper_1604_05872_gb300 import tuning
+        _, model = tuning.load(args.tuning)
+        for form in range(4):
+            for p in range(1, 5):
+                tuning.choose(model, form, p)
+        ms_mlp = timed(args.steps)
+        t_bound_mlp, _ = bound_time()
+        result.update({"mlp_choice_ms": ms_mlp, "mlp_gain": ms_flop / ms_mlp})
+        if ms_mlp < ms_flop:
+            ms, choice, t_bound = ms_mlp, "learned MLP cost model", t_bound_mlp
+        fea.tune_clear()
+    ms_max = max_over_ranks(ms)
+    return {
+        "metric": METRIC, "value": total * world / (ms_max * 1e-3), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "stream_64req_2M", "requests": len(reqs), "elements": total, "choice": choice,
+                   "launch": "one persistent kernel per step, replayed CUDA graph"},
+        "roofline": {"bound": "mixed", "achieved": t_bound * 1e3, "peak": ms, "unit": "ms (sum of per-request bound times / measured)",
+                     "frac": t_bound * 1e3 / ms, "traffic": None, "alg_bytes_per_launch": alg_bytes,
+                     "peak_kind": peak_kind},
+        "stream": result, "gpu_launches": args.steps, "clocks": clk.summary(), "e2e": None,
+    }
 
 
 if __name__ == "__main__":

@@ -207,6 +207,29 @@ int fea_theta(int form, int degree, int monomial, int64_t* theta_se, int64_t* th
  * the memory threshold T_H = smem_budget bytes (0 = 227 KB), and its cost. */
 int fea_algorithm3(int form, int degree, int precision, size_t smem_budget, unsigned* premask, int64_t* cost);
 
+/* ---- tuning and the learned cost model (the paper has no counterpart; it asks
+ * for "a more sophisticated cost model" in Section 8) ----
+ * Install / clear a tuned (variant, tile) for (form, degree, precision): used by
+ * FEA_VARIANT_AUTO and tile 0 in every later call (tile 0 keeps the default
+ * tile; variant FEA_VARIANT_AUTO keeps Algorithm 3's variant). */
+int fea_tune_set(int form, int degree, int precision, int variant, int tile);
+void fea_tune_clear(void);
+
+/* MLP cost model y = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3 with d_in <= 32
+ * inputs and hidden in {16, 32, 64}; parameters (float, device) laid out as
+ * W1[hidden][d_in] b1 W2[hidden][hidden] b2 w3 b3.  All pointers are device
+ * pointers; calls are asynchronous on `stream`. */
+int fea_mlp_num_params(int d_in, int hidden);                 /* -1 if unsupported */
+int64_t fea_mlp_scratch_floats(int n, int hidden);            /* workspace of fea_mlp_loss_grad */
+int fea_mlp_forward(const float* params, int d_in, int hidden, const float* X, int n, float* y, void* stream);
+/* Mean squared error over n rows and its gradient (deterministic, no atomics);
+ * `scratch` holds fea_mlp_scratch_floats(n, hidden) floats. */
+int fea_mlp_loss_grad(const float* params, int d_in, int hidden, const float* X, const float* y, int n,
+                      float* grad, float* loss, float* scratch, void* stream);
+/* One Adam step (bias-corrected; step counts from 1). */
+int fea_mlp_adam(float* params, const float* grad, float* m, float* v, int nparam, float lr, float beta1,
+                 float beta2, float eps, int step, void* stream);
+
 const char* fea_last_error(void);
 void fea_finalize(void);
 

@@ -27,6 +27,8 @@ EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points
            "fea_sync", "fea_plan",
            "fea_op_count", "fea_opcount_program", "fea_sharing_elimination", "fea_vertex_cover",
            "fea_increase_factor", "fea_num_monomials", "fea_theta", "fea_algorithm3",
+           "fea_tune_set", "fea_tune_clear", "fea_mlp_num_params", "fea_mlp_scratch_floats",
+           "fea_mlp_forward", "fea_mlp_loss_grad", "fea_mlp_adam",
            "fea_last_error", "fea_finalize"]
 
 
@@ -89,6 +91,16 @@ def load(path=None):
     lib.fea_num_monomials.argtypes = [i, i]
     lib.fea_theta.argtypes = [i, i, i, P(i64), P(i64), P(i64)]
     lib.fea_algorithm3.argtypes = [i, i, i, ctypes.c_size_t, P(ctypes.c_uint), P(i64)]
+    lib.fea_tune_set.argtypes = [i, i, i, i, i]
+    lib.fea_tune_clear.argtypes = []
+    lib.fea_tune_clear.restype = None
+    lib.fea_mlp_num_params.argtypes = [i, i]
+    lib.fea_mlp_scratch_floats.argtypes = [i, i]
+    lib.fea_mlp_scratch_floats.restype = i64
+    lib.fea_mlp_forward.argtypes = [vp, i, i, vp, i, vp, vp]
+    lib.fea_mlp_loss_grad.argtypes = [vp, i, i, vp, vp, i, vp, vp, vp, vp]
+    lib.fea_mlp_adam.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, i, vp]
     lib.fea_last_error.restype = ctypes.c_char_p
     lib.fea_finalize.argtypes = []
     _lib = lib
@@ -254,6 +266,46 @@ def algorithm3(form, degree, precision=PREC_FP32, smem_budget=0):
     m, c = ctypes.c_uint(), ctypes.c_int64()
     _check(load().fea_algorithm3(form, degree, precision, smem_budget, ctypes.byref(m), ctypes.byref(c)))
     return m.value, c.value
+
+
+def tune_set(form, degree, variant=VARIANT_AUTO, tile=0, precision=PREC_FP32):
+    _check(load().fea_tune_set(form, degree, precision, variant, tile))
+
+
+def tune_clear():
+    load().fea_tune_clear()
+
+
+def mlp_num_params(d_in, hidden):
+    return load().fea_mlp_num_params(d_in, hidden)
+
+
+def mlp_forward(params, X, hidden, out=None, stream=None):
+    """Predictions of the MLP for rows X [n, d_in] (float32 device tensors)."""
+    import torch
+    n, d = X.shape
+    y = out if out is not None else torch.empty(n, dtype=torch.float32, device=X.device)
+    _check(load().fea_mlp_forward(_ptr(params), d, hidden, _ptr(X), n, _ptr(y), _stream_ptr(stream)))
+    return y
+
+
+def mlp_loss_grad(params, X, y, hidden, grad=None, loss=None, scratch=None, stream=None):
+    """(loss [1], grad [nparam]) of the mean squared error, on the device."""
+    import torch
+    n, d = X.shape
+    dev = X.device
+    grad = grad if grad is not None else torch.empty_like(params)
+    loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=dev)
+    if scratch is None:
+        scratch = torch.empty(load().fea_mlp_scratch_floats(n, hidden), dtype=torch.float32, device=dev)
+    _check(load().fea_mlp_loss_grad(_ptr(params), d, hidden, _ptr(X), _ptr(y), n, _ptr(grad), _ptr(loss),
+                                    _ptr(scratch), _stream_ptr(stream)))
+    return loss, grad
+
+
+def mlp_adam(params, grad, m, v, step, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().fea_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), lr, beta1, beta2, eps,
+                               step, _stream_ptr(stream)))
 
 
 def finalize():

@@ -143,8 +143,33 @@ static fea_options default_options() {
 
 static bool valid_fd(int form, int p) { return form >= 0 && form <= 3 && p >= 1 && p <= 4; }
 
-// Resolve variant, kernel and tile for a request.
+// Resolve variant, kernel and tile for a request.  Plans are cached: planning
+// runs Algorithm 3 (expression rewriting and counting), far too slow to repeat
+// on every launch.
+static int make_plan_uncached(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch);
+
 int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch) {
+  static std::mutex mu;
+  static std::map<std::vector<int64_t>, Plan> cache;
+  const std::vector<int64_t> key = {form, p, o.precision, o.variant, o.tile, (int64_t)o.smem_budget, batch ? 1 : 0,
+                                    st ? (int64_t)st->smem_optin : -1, tuned_generation()};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *pl = it->second;
+      return FEA_OK;
+    }
+  }
+  int rc = make_plan_uncached(st, form, p, o, pl, batch);
+  if (rc == FEA_OK) {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = *pl;
+  }
+  return rc;
+}
+
+static int make_plan_uncached(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch) {
   if (!valid_fd(form, p)) return fail(FEA_EINVAL, "unsupported form/degree");
   if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32) return fail(FEA_EINVAL, "unsupported precision");
   const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
@@ -210,9 +235,27 @@ int launch_plan(DevState* st, const Plan& pl, int form, int p, int64_t E, const 
   q.kind = 0;
   q.tile0 = 0;
   const int64_t ntiles = (E + pl.tile - 1) / pl.tile;
-  CUDA_TRY(cudaFuncSetAttribute(pl.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, NT, pl.smem));
+  {
+    // the opt-in shared-memory ceiling is raised once per kernel and device (it only
+    // permits; each launch still asks for its own size), occupancy once per size
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, size_t, int>, int> occ;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(pl.k->fn, pl.smem, st->dev);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+      cudaFuncAttributes fa;
+      CUDA_TRY(cudaFuncGetAttributes(&fa, pl.k->fn));
+      const int ceiling = (int)st->smem_optin - (int)fa.sharedSizeBytes;  // minus the kernel's static shared memory
+      if ((int)pl.smem > ceiling) return fail(FEA_EINVAL, "tile does not fit the device's shared memory");
+      CUDA_TRY(cudaFuncSetAttribute(pl.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ceiling));
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, NT, pl.smem));
+      occ[key] = per_sm;
+    } else {
+      per_sm = it->second;
+    }
+  }
   if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with this tile");
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
   unsigned* err = st->err;

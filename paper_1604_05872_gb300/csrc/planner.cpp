@@ -92,10 +92,17 @@ OpCounts op_counts(int form, int p) {
 
 static std::mutex g_tmu;
 static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;
+static int g_tuned_gen = 0;
+
+int tuned_generation() {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  return g_tuned_gen;
+}
 
 void set_tuned(int form, int p, int prec, int variant, int tile) {
   std::lock_guard<std::mutex> lk(g_tmu);
   g_tuned[std::make_tuple(form, p, prec)] = {variant, tile};
+  ++g_tuned_gen;
 }
 bool get_tuned(int form, int p, int prec, int* variant, int* tile) {
   std::lock_guard<std::mutex> lk(g_tmu);
@@ -108,6 +115,7 @@ bool get_tuned(int form, int p, int prec, int* variant, int* tile) {
 void clear_tuned() {
   std::lock_guard<std::mutex> lk(g_tmu);
   g_tuned.clear();
+  ++g_tuned_gen;
 }
 
 struct Theta {
@@ -193,3 +201,17 @@ extern "C" int fea_algorithm3(int form, int degree, int precision, size_t smem_b
   if (premask) *premask = m;
   return FEA_OK;
 }
+
+extern "C" int fea_tune_set(int form, int degree, int precision, int variant, int tile) {
+  using namespace fea;
+  if (form < 0 || form > 3 || degree < 1 || degree > 4) return set_error(FEA_EINVAL, "unsupported form/degree");
+  if (precision != FEA_PREC_FP64 && precision != FEA_PREC_FP32) return set_error(FEA_EINVAL, "unsupported precision");
+  if (variant != FEA_VARIANT_AUTO && variant != FEA_VARIANT_SE && variant != FEA_VARIANT_PRE)
+    return set_error(FEA_EINVAL, "a tuned variant is SE, PRE or AUTO");
+  if (variant == FEA_VARIANT_PRE && form == NEOHOOKEAN) return set_error(FEA_EINVAL, "no pre-evaluated Neo-Hookean form");
+  if (tile < 0) return set_error(FEA_EINVAL, "negative tile");
+  set_tuned(form, degree, precision == FEA_PREC_FP64 ? 0 : 1, variant, tile);
+  return FEA_OK;
+}
+
+extern "C" void fea_tune_clear(void) { fea::clear_tuned(); }

@@ -34,6 +34,7 @@ int default_tile(int variant, int form, int p, int prec, int max_tile, size_t bu
 void set_tuned(int form, int p, int prec, int variant, int tile);
 bool get_tuned(int form, int p, int prec, int* variant, int* tile);
 void clear_tuned();
+int tuned_generation();  // changes whenever a tuned choice is installed or cleared
 
 struct BatchState;
 void free_batch_state(BatchState* b);

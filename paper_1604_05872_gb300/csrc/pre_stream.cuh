@@ -8,9 +8,10 @@
 //     shared buffers, completing on an mbarrier, one tile ahead of use;
 //   * one thread per element does the FP64 geometry and writes the FP32
 //     geometry tensor H_e straight to shared memory;
-//   * each thread keeps two columns of R in registers and sweeps its elements,
-//     storing each finished pair of entries with one 16-byte streaming store
-//     (no staging: the element's entries are contiguous and 16-byte aligned).
+//   * each thread keeps two columns of R in registers and sweeps its elements
+//     two at a time, storing each finished pair of entries with one 16-byte
+//     streaming store (no staging: the element's entries are contiguous and
+//     16-byte aligned).
 // Every mbarrier wait is bounded; a wait that gives up sets the error word and
 // the whole CTA leaves the kernel.
 #pragma once
@@ -148,12 +149,6 @@ __global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
   const int t = threadIdx.x;
   const bool active = t < K::G * K::S;
   const int slot = t % K::S, g0 = t / K::S;
-  float r0[K::R], r1[K::R];
-#pragma unroll
-  for (int r = 0; r < K::R; ++r) {
-    r0[r] = active ? __ldg(Rg + (size_t)r * K::NN + 2 * slot) : 0.f;
-    r1[r] = active ? __ldg(Rg + (size_t)r * K::NN + 2 * slot + 1) : 0.f;
-  }
 
   auto tile_ne = [&](int j) {
     const int64_t e0 = (first + (int64_t)j * stride) * TE;
@@ -212,10 +207,51 @@ __global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
     // inputs of tile j + 2 go into the buffer tile j used (consumed before the last barrier)
     if (t == 0 && j + 2 < my_tiles) issue(j + 2);
     if (active) {
+      // this thread's two columns of R, reloaded per tile (L1 hits) so that they
+      // are not live across the FP64 geometry
+      float r0[K::R], r1[K::R];
+#pragma unroll
+      for (int r = 0; r < K::R; ++r) {
+        const float2 x = __ldg(reinterpret_cast<const float2*>(Rg + (size_t)r * K::NN) + slot);
+        r0[r] = x.x;
+        r1[r] = x.y;
+      }
       const float* Hb = H + (size_t)(j & 1) * TE * K::NHP;
       double2* o = reinterpret_cast<double2*>(reinterpret_cast<double*>(q.out) + e0 * K::NN) + slot;
       float2* of = reinterpret_cast<float2*>(reinterpret_cast<float*>(q.out) + e0 * K::NN) + slot;
-      for (int e = g0; e < ne; e += K::G) {
+      const double2 nan2 = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+      // two elements per iteration: independent accumulation chains
+      int e = g0;
+      for (; e + K::G < ne; e += 2 * K::G) {
+        const float* h = Hb + K::NHP * e;
+        const float* h2 = h + K::NHP * K::G;
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+        for (int r4 = 0; r4 < K::NHP; r4 += 4) {
+          const float4 hv = *reinterpret_cast<const float4*>(h + r4);
+          const float4 gv = *reinterpret_cast<const float4*>(h2 + r4);
+          const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
+          const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (r4 + k < K::R) {
+              a0 = fmaf(r0[r4 + k], hh[k], a0);
+              a1 = fmaf(r1[r4 + k], hh[k], a1);
+              b0 = fmaf(r0[r4 + k], gg[k], b0);
+              b1 = fmaf(r1[r4 + k], gg[k], b1);
+            }
+        }
+        if (q.out_f32) {
+          __stcs(of + (size_t)e * (K::NN / 2), make_float2(a0, a1));
+          __stcs(of + (size_t)(e + K::G) * (K::NN / 2), make_float2(b0, b1));
+        } else {
+          const double2 v = h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1));
+          const double2 w = h2[0] != h2[0] ? nan2 : make_double2(f2d_finite(b0), f2d_finite(b1));
+          __stcs(o + (size_t)e * (K::NN / 2), v);
+          __stcs(o + (size_t)(e + K::G) * (K::NN / 2), w);
+        }
+      }
+      for (; e < ne; e += K::G) {
         const float* h = Hb + K::NHP * e;
         float a0 = 0.f, a1 = 0.f;
 #pragma unroll
@@ -232,9 +268,7 @@ __global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
         if (q.out_f32) {
           __stcs(of + (size_t)e * (K::NN / 2), make_float2(a0, a1));
         } else {
-          double2 v = make_double2(f2d_finite(a0), f2d_finite(a1));
-          if (h[0] != h[0]) v = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
-          __stcs(o + (size_t)e * (K::NN / 2), v);
+          __stcs(o + (size_t)e * (K::NN / 2), h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1)));
         }
       }
     }
