@@ -137,3 +137,12 @@ def stream_requests(seed=SEED, nreq=64, total=2_000_000, lo=1_000, hi=200_000):
     forms = rng.integers(0, 4, size=nreq)
     degrees = rng.integers(1, 5, size=nreq)
     return [(int(f), int(d), int(s)) for f, d, s in zip(forms, degrees, sizes)]
+
+
+def shard(E, rank, world):
+    """Contiguous element range [start, start + count) of one rank: the element
+    loop is order-free (Definition 6), so ranks assemble disjoint ranges with no
+    exchange; the first E % world ranks take one element more."""
+    base, extra = divmod(E, world)
+    start = rank * base + min(rank, extra)
+    return start, base + (1 if rank < extra else 0)
