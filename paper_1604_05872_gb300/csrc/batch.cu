@@ -21,6 +21,8 @@
 #include "planner.h"
 #include "pre.cuh"
 #include "se.cuh"
+#include "se_vec.cuh"
+#include "pre_vec.cuh"
 
 namespace fea {
 
@@ -62,15 +64,20 @@ __global__ void __launch_bounds__(NT) batch_kernel(const Req* __restrict__ reqs,
     const unsigned dyn = dynamic_smem_bytes();
     switch (q.kind) {
 #define SEK(F, P) case (F) * 4 + (P) - 1: run_one<SeTile<F, P, float>>(q, t, smem_raw, err, dyn); break;
+#define SEVK(F, P) case (F) * 4 + (P) - 1: run_one<SeVecTile<F, P, float>>(q, t, smem_raw, err, dyn); break;
 #define PREK(F, P) case 16 + (F) * 4 + (P) - 1: run_one<PreTile<F, P, float>>(q, t, smem_raw, err, dyn); break;
       SEK(0, 1) SEK(0, 2) SEK(0, 3) SEK(0, 4)
       SEK(1, 1) SEK(1, 2) SEK(1, 3) SEK(1, 4)
-      SEK(2, 1) SEK(2, 2) SEK(2, 3) SEK(2, 4)
-      SEK(3, 1) SEK(3, 2) SEK(3, 3) SEK(3, 4)
+      SEVK(2, 1) SEVK(2, 2) SEVK(2, 3) SEVK(2, 4)
+      SEVK(3, 1) SEVK(3, 2) SEVK(3, 3) SEVK(3, 4)
       PREK(0, 1) PREK(0, 2) PREK(0, 3) PREK(0, 4)
       PREK(1, 1) PREK(1, 2) PREK(1, 3) PREK(1, 4)
-      PREK(2, 1) PREK(2, 2) PREK(2, 3) PREK(2, 4)
+      case 16 + 2 * 4 + 0: run_one<PreVecTile<1, float>>(q, t, smem_raw, err, dyn); break;
+      case 16 + 2 * 4 + 1: run_one<PreVecTile<2, float>>(q, t, smem_raw, err, dyn); break;
+      case 16 + 2 * 4 + 2: run_one<PreVecTile<3, float>>(q, t, smem_raw, err, dyn); break;
+      case 16 + 2 * 4 + 3: run_one<PreVecTile<4, float>>(q, t, smem_raw, err, dyn); break;
 #undef SEK
+#undef SEVK
 #undef PREK
       default: break;
     }

@@ -2,6 +2,7 @@
 #include "launch.cuh"
 #include "pre.cuh"
 #include "pre_stream.cuh"
+#include "pre_vec.cuh"
 
 namespace fea {
 
@@ -14,20 +15,24 @@ KernelInfo stream_info() {
 
 #define PRE(F, P) make_info<PreTile<F, P, float>>(V_PRE, F, P, 1), make_info<PreTile<F, P, double>>(V_PRE, F, P, 0)
 #define PRES(F, P) stream_info<F, P>(), make_info<PreTile<F, P, double>>(V_PRE, F, P, 0)
+#define PREV(P) make_info<PreVecTile<P, float>>(V_PRE, 2, P, 1), make_info<PreVecTile<P, double>>(V_PRE, 2, P, 0)
 const KernelInfo kPreKernels[] = {
     PRES(0, 1), PRES(0, 2), PRES(0, 3), PRE(0, 4),
     PRES(1, 1), PRES(1, 2), PRES(1, 3), PRE(1, 4),
-    PRE(2, 1), PRE(2, 2), PRE(2, 3), PRE(2, 4),
+    PREV(1), PREV(2), PREV(3), PREV(4),
 };
 #undef PRE
 #undef PRES
+#undef PREV
 const int kNumPreKernels = sizeof(kPreKernels) / sizeof(kPreKernels[0]);
 
 // The FP32 tile functions the batched kernel dispatches to (their shared-memory
 // layouts and tile limits plan the batch).
 #define PT(F, P) make_info<PreTile<F, P, float>>(V_PRE, F, P, 1)
+#define PTV(P) make_info<PreVecTile<P, float>>(V_PRE, 2, P, 1)
 const KernelInfo kPreTileF32[] = {PT(0, 1), PT(0, 2), PT(0, 3), PT(0, 4), PT(1, 1), PT(1, 2),
-                                  PT(1, 3), PT(1, 4), PT(2, 1), PT(2, 2), PT(2, 3), PT(2, 4)};
+                                  PT(1, 3), PT(1, 4), PTV(1), PTV(2), PTV(3), PTV(4)};
+#undef PTV
 #undef PT
 const int kNumPreTileF32 = sizeof(kPreTileF32) / sizeof(kPreTileF32[0]);
 
