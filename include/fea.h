@@ -167,6 +167,10 @@ int fea_sync(void* stream);
 /* Plan for (form, degree, options) without launching anything. */
 int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info);
 
+/* The same plan ignoring tuned choices: the paper's choice by operation count
+ * (Algorithm 3's variant and the shared-memory tile rule). */
+int fea_plan_flop(int form, int degree, const fea_options* opt, fea_plan_info* info);
+
 /* Operation counts per element (Definition 8 counting: adds and products, an
  * FMA counts 2) of the plain nest and of `variant` (AUTO = Algorithm 3 pick). */
 int fea_op_count(int form, int degree, int variant, int64_t* naive_flops, int64_t* opt_flops);

@@ -24,7 +24,7 @@ VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_noalloc",
-           "fea_sync", "fea_plan",
+           "fea_sync", "fea_plan", "fea_plan_flop",
            "fea_op_count", "fea_opcount_program", "fea_sharing_elimination", "fea_vertex_cover",
            "fea_increase_factor", "fea_num_monomials", "fea_theta", "fea_algorithm3",
            "fea_tune_set", "fea_tune_clear", "fea_mlp_num_params", "fea_mlp_scratch_floats",
@@ -81,6 +81,7 @@ def load(path=None):
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
+    lib.fea_plan_flop.argtypes = [i, i, P(Options), P(PlanInfo)]
     lib.fea_op_count.argtypes = [i, i, i, P(i64), P(i64)]
     cp = ctypes.c_char_p
     lib.fea_opcount_program.argtypes = [cp, cp, P(i64)]
@@ -209,6 +210,14 @@ def plan(form, degree, precision=PREC_FP32, out_f32=False, variant=VARIANT_AUTO,
     info = PlanInfo()
     o = options(precision, out_f32, variant, tile, smem_budget)
     _check(load().fea_plan(form, degree, ctypes.byref(o), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+
+def plan_flop(form, degree, precision=PREC_FP32, out_f32=False, smem_budget=0):
+    """The plan without tuned choices: Algorithm 3's variant and the default tile."""
+    info = PlanInfo()
+    o = options(precision, out_f32, VARIANT_AUTO, 0, smem_budget)
+    _check(load().fea_plan_flop(form, degree, ctypes.byref(o), ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
 
 

@@ -146,13 +146,19 @@ static bool valid_fd(int form, int p) { return form >= 0 && form <= 3 && p >= 1 
 // Resolve variant, kernel and tile for a request.  Plans are cached: planning
 // runs Algorithm 3 (expression rewriting and counting), far too slow to repeat
 // on every launch.
-static int make_plan_uncached(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch);
+static int make_plan_uncached(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch,
+                              bool use_tuned);
 
+int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch, bool use_tuned);
 int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch) {
+  return make_plan(st, form, p, o, pl, batch, true);
+}
+
+int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch, bool use_tuned) {
   static std::mutex mu;
   static std::map<std::vector<int64_t>, Plan> cache;
   const std::vector<int64_t> key = {form, p, o.precision, o.variant, o.tile, (int64_t)o.smem_budget, batch ? 1 : 0,
-                                    st ? (int64_t)st->smem_optin : -1, tuned_generation()};
+                                    st ? (int64_t)st->smem_optin : -1, use_tuned ? tuned_generation() : -1};
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -161,7 +167,7 @@ int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, boo
       return FEA_OK;
     }
   }
-  int rc = make_plan_uncached(st, form, p, o, pl, batch);
+  int rc = make_plan_uncached(st, form, p, o, pl, batch, use_tuned);
   if (rc == FEA_OK) {
     std::lock_guard<std::mutex> lk(mu);
     cache[key] = *pl;
@@ -169,14 +175,15 @@ int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, boo
   return rc;
 }
 
-static int make_plan_uncached(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch) {
+static int make_plan_uncached(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch,
+                              bool use_tuned) {
   if (!valid_fd(form, p)) return fail(FEA_EINVAL, "unsupported form/degree");
   if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32) return fail(FEA_EINVAL, "unsupported precision");
   const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
   const size_t limit = st ? st->smem_optin : 232448;
   const size_t budget = o.smem_budget ? std::min(o.smem_budget, limit) : limit;
   int variant = o.variant;
-  if (variant == FEA_VARIANT_AUTO) variant = choose_variant(form, p, prec, budget);
+  if (variant == FEA_VARIANT_AUTO) variant = choose_variant(form, p, prec, budget, use_tuned);
   if (variant == FEA_VARIANT_NAIVE && prec != 0) return fail(FEA_EINVAL, "the plain variant is FP64 only");
   if (variant == FEA_VARIANT_PRE && pre_terms(form, p) == 0)
     return fail(FEA_EINVAL, "pre-evaluation does not apply to this form (integrand not polynomial)");
@@ -185,7 +192,8 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
   const int Q = rule_points(rule_index(form, p));
   int TE = o.tile;
   if (TE < 0) return fail(FEA_EINVAL, "negative tile");
-  if (TE == 0) TE = default_tile(variant, form, p, prec, k->max_tile, budget, Q, k->smem);
+  // tuned tiles were measured on the standalone kernels; the batch keeps its own rule
+  if (TE == 0) TE = default_tile(variant, form, p, prec, k->max_tile, budget, Q, k->smem, use_tuned && !batch);
   if (TE < 1 || TE > k->max_tile) return fail(FEA_EINVAL, "tile out of range for this kernel");
   const size_t smem = k->smem(TE, Q);
   if (smem > budget) return fail(FEA_EINVAL, "tile does not fit the shared-memory budget (Constraint 2)");
@@ -429,7 +437,7 @@ int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_opti
 }
 int fea_sync(void* stream) { return sync_impl(stream); }
 
-int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info) {
+static int plan_impl(int form, int degree, const fea_options* opt, fea_plan_info* info, bool use_tuned) {
   if (!info) return fail(FEA_EINVAL, "info is NULL");
   const fea_options o = opt ? *opt : default_options();
   DevState* st = nullptr;
@@ -441,7 +449,7 @@ int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info) 
     cudaGetLastError();
   }
   Plan pl;
-  int rc = make_plan(st, form, degree, o, &pl, false);
+  int rc = make_plan(st, form, degree, o, &pl, false, use_tuned);
   if (rc) return rc;
   OpCounts oc = op_counts(form, degree);
   info->variant = pl.variant;
@@ -457,6 +465,14 @@ int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info) 
   const int n = local_dim(form, degree);
   info->bytes = 96 + 8 * (int64_t)coeff_len(form, degree) + (int64_t)n * n * (o.out_f32 ? 4 : 8);
   return FEA_OK;
+}
+
+int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info) {
+  return plan_impl(form, degree, opt, info, true);
+}
+
+int fea_plan_flop(int form, int degree, const fea_options* opt, fea_plan_info* info) {
+  return plan_impl(form, degree, opt, info, false);
 }
 
 int fea_op_count(int form, int degree, int variant, int64_t* naive_flops, int64_t* opt_flops) {

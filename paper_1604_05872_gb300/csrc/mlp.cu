@@ -40,16 +40,16 @@ constexpr int kMaxD = 32;
 
 template <int H>
 __device__ __forceinline__ float forward_row(const float* p, const Off& o, int D, const float* x, float* a1, float* a2) {
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < H; ++i) {
     float z = p[o.b1 + i];
     for (int d = 0; d < D; ++d) z = fmaf(p[o.W1 + i * D + d], x[d], z);
     a1[i] = tanhf(z);
   }
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < H; ++i) {
     float z = p[o.b2 + i];
-#pragma unroll
+#pragma unroll 8
     for (int j = 0; j < H; ++j) z = fmaf(p[o.W2 + i * H + j], a1[j], z);
     a2[i] = tanhf(z);
   }
@@ -95,10 +95,10 @@ __global__ void mlp_rows_kernel(const float* __restrict__ params, int D, const f
   float dz2[H];
 #pragma unroll
   for (int i = 0; i < H; ++i) dz2[i] = g * sp[o.w3 + i] * (1.0f - a2[i] * a2[i]);
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < H; ++j) {
     float da = 0.f;
-#pragma unroll
+#pragma unroll 8
     for (int i = 0; i < H; ++i) da = fmaf(sp[o.W2 + i * H + j], dz2[i], da);
     s[2 * H + j] = da * (1.0f - a1[j] * a1[j]);  // dz1
   }

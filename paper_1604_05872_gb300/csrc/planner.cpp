@@ -51,13 +51,14 @@ static std::vector<MonoCost> monomials(int form, int p) {
       m.push_back({Q * (2 * ns + ns + 1 + 2 * nn), ns + 2 * ns * nn, ns * ns * ns});
       break;
     case ELASTICITY:
-      // SE: gradients, mu_q/lam_q (16), D (81 x 4), left operands 45 per row, 3 FMA per entry
-      // PRE: geometry tensor 324 x 8, 36 terms per entry
-      m.push_back({Q * (grad + 18 + 324 + 45 * n + 6 * nn), 324 * 8 + 72 * nn, 36 * ns * ns});
+      // SE (factorised tangent): gradients, mu_q/lam_q (18), 24 FMA per (a, b) block
+      // PRE followed by sharing elimination: M (54), then per (a, b) X and L (72 FMA),
+      // tr(M X) (9), X^T + L (9), adj^T Z adj (54) and the scaling (9)
+      m.push_back({Q * (grad + 18 + 48 * ns * ns), 54 + 306 * ns * ns, 36 * ns * ns});
       break;
     case NEOHOOKEAN:
-      // SE: gradients twice (F and contraction), F (18 ns), D (81 x 10), left operands, 3 FMA per entry
-      m.push_back({Q * (2 * grad + 18 * ns + 810 + 45 * n + 6 * nn), -1, 0});
+      // SE: gradients twice (F and contraction), F (18 ns), Y = F^-T G (15 ns), 24 FMA per (a, b) block
+      m.push_back({Q * (2 * grad + 18 * ns + 15 * ns + 6 + 48 * ns * ns), -1, 0});
       break;
   }
   return m;
@@ -161,9 +162,9 @@ unsigned algorithm3(int form, int p, int prec, size_t budget, int64_t* best_cost
   return best;
 }
 
-int choose_variant(int form, int p, int prec, size_t budget) {
+int choose_variant(int form, int p, int prec, size_t budget, bool use_tuned) {
   int v = 0, t = 0;
-  if (get_tuned(form, p, prec, &v, &t) && v != FEA_VARIANT_AUTO) return v;
+  if (use_tuned && get_tuned(form, p, prec, &v, &t) && v != FEA_VARIANT_AUTO) return v;
   if (form == NEOHOOKEAN) return FEA_VARIANT_SE;
   const unsigned mask = algorithm3(form, p, prec, budget, nullptr);
   const int nm = num_monomials(form, p);
@@ -176,9 +177,9 @@ int choose_variant(int form, int p, int prec, size_t budget) {
 }
 
 int default_tile(int variant, int form, int p, int prec, int max_tile, size_t budget, int Q,
-                 size_t (*smem)(int, int)) {
+                 size_t (*smem)(int, int), bool use_tuned) {
   int v = 0, t = 0;
-  if (get_tuned(form, p, prec, &v, &t) && t > 0 && t <= max_tile && smem(t, Q) <= budget) return t;
+  if (use_tuned && get_tuned(form, p, prec, &v, &t) && t > 0 && t <= max_tile && smem(t, Q) <= budget) return t;
   // target a few resident CTAs per SM: about 48 KB of shared memory per tile
   const size_t target = std::min<size_t>(budget, 48 * 1024);
   int best = 1;

@@ -26,9 +26,9 @@ OpCounts op_counts(int form, int p);
 // Algorithm 3 (Section 4.1) on the form's monomials with the memory threshold
 // T_H = `budget` bytes of shared memory: returns FEA_VARIANT_SE or _PRE.
 // Tuned choices installed with set_tuned() take precedence.
-int choose_variant(int form, int p, int prec, size_t budget);
+int choose_variant(int form, int p, int prec, size_t budget, bool use_tuned = true);
 int default_tile(int variant, int form, int p, int prec, int max_tile, size_t budget, int Q,
-                 size_t (*smem)(int, int));
+                 size_t (*smem)(int, int), bool use_tuned = true);
 
 // Tuned overrides (autotuner / learned cost model), keyed by (form, p, prec).
 void set_tuned(int form, int p, int prec, int variant, int tile);

@@ -1,14 +1,22 @@
-// Pre-evaluated variant for elasticity, register-blocked (Algorithm 2):
+// Pre-evaluated variant for elasticity (Algorithm 2), followed by sharing
+// elimination on the pre-evaluated expression (Algorithm 3, step 5).
 //
-//   A_e[3a+c][3b+d] = sum_r R_r[a][b] H_e[r][c][d],   r = (k, al, be), 36 terms
+// With pre-evaluated tables R_(k,al,be)[a][b] = int Phi1_k dPhi_a/dX_al dPhi_b/dX_be
+// (36 per (a, b)) and the adjugate adj = det(J) J^-1:
 //
-// with H_e[(k,al,be)][c][d] = |det J| (mu_k (d_cd M_al,be + Ji_al,d Ji_be,c) + lam_k Ji_al,c Ji_be,d)
-// formed once per element from the FP64 geometry.  Each thread owns one test
-// function a and up to five trial functions b of one element (45 accumulators):
-// per term r it reads the element's 9 geometry entries (three 16-byte shared
-// loads, shared by the element's threads) and five R_r[a][b] values (L1), and
-// issues 45 FMAs.  Results are staged in shared memory and written with
-// coalesced 16-byte stores.
+//   A_e[(a,c)][(b,d)] = sum_(k,al,be) R_(k,al,be)[a][b] H_e[(k,al,be)][c][d]
+//   H = (mu_k (d_cd M_al,be + adj_al,d adj_be,c) + lam_k adj_al,c adj_be,d) / |det J|,   M = adj adj^T
+//
+// Factorising the sums over k and (al, be) out of the (c, d) block gives
+//
+//   X = sum_k mu_k R_k,  L = sum_k lam_k R_k                     (3x3 each, per a, b)
+//   A_e[(a,.)][(b,.)] = ( tr(M X) I + adj^T (X^T + L) adj ) / |det J|
+//
+// 144 FMA per (a, b) block instead of 324 for the plain geometry-tensor GEMV.
+// Each thread owns one (a, b) pair, keeps its 36 R values in registers and
+// sweeps the tile's elements, reading the element's adjugate, M and
+// coefficients with broadcast shared loads; results are staged in shared memory
+// and written with coalesced 16-byte stores.
 #pragma once
 #include "common.cuh"
 
@@ -20,19 +28,14 @@ struct PreVecTile {
   static constexpr int NS = nbasis_c(P);
   static constexpr int N = 3 * NS;
   static constexpr int NN = N * N;
-  static constexpr int R = 36;
-  static constexpr int HB = 12;                 // H entries per term (9 + pad)
+  static constexpr int S = NS * NS;              // (a, b) slots
   static constexpr int CLEN = 8;
-  static constexpr int BB = 5;
-  static constexpr int NB = (NS + BB - 1) / BB;
-  static constexpr int TPE = NS * NB;
-  static constexpr int GEO = 12;
+  static constexpr int GEO = 32;                 // adj[9], M[9], mu[4], lam[4], 1/|det|, pad
 
-  FEA_HD static int max_tile() { return NT / TPE; }
+  FEA_HD static int max_tile() { return 64; }
   FEA_HD static size_t off_c(int TE) { return round_up_sz((size_t)TE * 12 * 8, 16); }
   FEA_HD static size_t off_geo(int TE) { return off_c(TE) + round_up_sz((size_t)TE * CLEN * 8, 16); }
-  FEA_HD static size_t off_h(int TE) { return off_geo(TE) + round_up_sz((size_t)TE * GEO * sizeof(T), 16); }
-  FEA_HD static size_t off_stage(int TE) { return off_h(TE) + round_up_sz((size_t)TE * R * HB * sizeof(T), 16); }
+  FEA_HD static size_t off_stage(int TE) { return off_geo(TE) + round_up_sz((size_t)TE * GEO * sizeof(T), 16); }
   FEA_HD static size_t smem(int TE, int Q) { (void)Q; return off_stage(TE) + round_up_sz((size_t)TE * NN * sizeof(T), 16); }
 
   __device__ static void tile(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
@@ -40,87 +43,74 @@ struct PreVecTile {
     double* xs = reinterpret_cast<double*>(sm);
     double* cs = reinterpret_cast<double*>(sm + off_c(TE));
     T* geo = reinterpret_cast<T*>(sm + off_geo(TE));
-    T* H = reinterpret_cast<T*>(sm + off_h(TE));
     T* stage = reinterpret_cast<T*>(sm + off_stage(TE));
-    const TabLayout L = tab_layout(q.Q, NS, R);
-    const T* Rg = reinterpret_cast<const T*>(q.tab) + L.offR;  // [r][a][b]
+    const TabLayout L = tab_layout(q.Q, NS, 36);
+    const T* Rg = reinterpret_cast<const T*>(q.tab) + L.offR;  // [(k,al,be)][a][b]
     const int tid = threadIdx.x;
 
     load_doubles<NT>(xs, q.coords + e0 * 12, ne * 12);
     load_doubles<NT>(cs, q.coeffs + e0 * CLEN, ne * CLEN);
     __syncthreads();
-    if (tid < ne) {  // FP64 geometry
+    if (tid < ne) {  // FP64 geometry; FP32 (or FP64) per-element record
       double adj[9];
       const double det = geometry_fp64(xs + 12 * tid, adj);
       const bool bad = !(fabs(det) > 0.0) || !isfinite(det);
       if (bad) flag_error(err, ERR_DEGENERATE);
       T* g = geo + GEO * tid;
-      const T nan = T(__int_as_float(0x7fc00000));
+      T a[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) g[k] = from_double<T>(adj[k]);
-      const T ad = from_double<T>(fabs(det));
-      g[9] = bad ? nan : ad;
-      g[10] = bad ? nan : T(1) / ad;
-    }
-    __syncthreads();
-    for (int w = tid; w < ne * R * HB; w += NT) {  // geometry tensors
-      const int e = w / (R * HB), h = w - e * (R * HB), rr = h / HB, cd = h - rr * HB;
-      T v = T(0);
-      if (cd < 9) {
-        const T* g = geo + GEO * e;
-        const double* c = cs + CLEN * e;
-        const int k = rr / 9, al = (rr / 3) % 3, be = rr % 3, cc = cd / 3, d = cd % 3;
-        const T M = g[3 * al] * g[3 * be] + g[3 * al + 1] * g[3 * be + 1] + g[3 * al + 2] * g[3 * be + 2];
-        const T mu = from_double<T>(c[k]), lam = from_double<T>(c[4 + k]);
-        v = (mu * ((cc == d ? M : T(0)) + g[3 * al + d] * g[3 * be + cc]) + lam * g[3 * al + cc] * g[3 * be + d]) * g[10];
-      }
-      H[w] = v;
+      for (int k = 0; k < 9; ++k) g[k] = a[k] = from_double<T>(adj[k]);
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be)
+          g[9 + 3 * al + be] = a[3 * al] * a[3 * be] + a[3 * al + 1] * a[3 * be + 1] + a[3 * al + 2] * a[3 * be + 2];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) g[18 + k] = from_double<T>(cs[CLEN * tid + k]);
+      const T nan = T(__int_as_float(0x7fc00000));
+      g[26] = bad ? nan : T(1) / from_double<T>(fabs(det));
     }
     __syncthreads();
 
-    const int te = tid / TPE, r0 = tid - te * TPE;
-    const int a = r0 / NB, b0 = (r0 - a * NB) * BB;
-    const int nb = NS - b0 < BB ? NS - b0 : BB;
-    if (te < ne) {
-      T acc[BB][9];
+    for (int s = tid; s < S; s += NT) {
+      const int a = s / NS, b = s - a * NS;
+      T R[36];
 #pragma unroll
-      for (int i = 0; i < BB; ++i)
+      for (int r = 0; r < 36; ++r) R[r] = __ldg(Rg + (size_t)r * S + s);
+      for (int e = 0; e < ne; ++e) {
+        const T* g = geo + GEO * e;
+        T X[9], Lm[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) acc[i][k] = T(0);
-      const T* h = H + (size_t)te * R * HB;
-      const T* rp = Rg + (size_t)a * NS + b0;
-#pragma unroll 4
-      for (int r = 0; r < R; ++r) {
-        T hv[12];
-        if constexpr (sizeof(T) == 4) {
-#pragma unroll
-          for (int k = 0; k < 12; k += 4) {
-            const float4 x = *reinterpret_cast<const float4*>(h + r * HB + k);
-            hv[k] = x.x; hv[k + 1] = x.y; hv[k + 2] = x.z; hv[k + 3] = x.w;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 10; k += 2) {
-            const double2 x = *reinterpret_cast<const double2*>(h + r * HB + k);
-            hv[k] = x.x; hv[k + 1] = x.y;
-          }
+        for (int k = 0; k < 9; ++k) {
+          X[k] = g[18] * R[k] + g[19] * R[9 + k] + g[20] * R[18 + k] + g[21] * R[27 + k];
+          Lm[k] = g[22] * R[k] + g[23] * R[9 + k] + g[24] * R[18 + k] + g[25] * R[27 + k];
         }
-        T rv[BB];
+        T tr = T(0);
 #pragma unroll
-        for (int i = 0; i < BB; ++i) rv[i] = i < nb ? __ldg(rp + (size_t)r * NS * NS + i) : T(0);
+        for (int k = 0; k < 9; ++k) tr = fma(g[9 + k], X[k], tr);
+        // Z = X^T + L;  P = Z adj;  A = adj^T P
+        T Pm[9];
 #pragma unroll
-        for (int i = 0; i < BB; ++i)
+        for (int al = 0; al < 3; ++al)
 #pragma unroll
-          for (int k = 0; k < 9; ++k) acc[i][k] = fma(rv[i], hv[k], acc[i][k]);
+          for (int d = 0; d < 3; ++d) {
+            T v = T(0);
+#pragma unroll
+            for (int be = 0; be < 3; ++be) v = fma(X[3 * be + al] + Lm[3 * al + be], g[3 * be + d], v);
+            Pm[3 * al + d] = v;
+          }
+        const T inv = g[26];
+        T* o = stage + (size_t)e * NN + (3 * a) * N + 3 * b;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            T v = c == d ? tr : T(0);
+#pragma unroll
+            for (int al = 0; al < 3; ++al) v = fma(g[3 * al + c], Pm[3 * al + d], v);
+            o[c * N + d] = v * inv;
+          }
       }
-      T* o = stage + (size_t)te * NN + (3 * a) * N + 3 * b0;
-#pragma unroll
-      for (int i = 0; i < BB; ++i)
-        if (i < nb)
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) o[c * N + 3 * i + d] = acc[i][3 * c + d];
     }
     __syncthreads();
     store_tile<NT, T>(q.out, e0 * NN, stage, ne * NN, q.out_f32);

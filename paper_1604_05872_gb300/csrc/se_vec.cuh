@@ -1,19 +1,22 @@
-// Sharing-elimination variant for the vector forms (elasticity, Neo-Hookean),
-// register-blocked.  Same arithmetic as SeTile (Section 3.2, Algorithm 1):
+// Sharing-elimination variant for the vector forms (elasticity, Neo-Hookean).
 //
-//   per point q:  G_a = J^-T grad Phi_a(X_q)                        (per e, a)
-//                 D[c,I][d,J] = s_q * tangent                        (per e)
-//                 L_(a,c)[d,J] = sum_I G_a^I D[c,I][d,J]             (per e, a, c)
-//                 A[(a,c)][(b,d)] += sum_J L_(a,c)[d,J] G_b^J        (3 FMA per entry)
+// Both tangents have the structure
+//   A[c,I][d,J] = mu d_cd d_IJ + alpha Fi_Jc Fi_Id + lam Fi_Ic Fi_Jd
+// (Neo-Hookean: Fi = F^-1, alpha = mu - lam ln det F, mu and lam constants;
+// elasticity: Fi = I, alpha = mu, with mu, lam the P1 fields at the point).
+// Factorising the test/trial contraction through it (Section 3.2: expansion,
+// factorisation and code motion of what depends on (e, q) or (e, q, a) only):
 //
-// Schedule: each thread owns one test function a and a chunk of up to five
-// trial functions b of one element, i.e. 5 x 9 accumulators in registers; per
-// point it loads L_(a,.) once (27 values) and G_b once per b, so every shared
-// load feeds several FMAs.  Pointwise data of all (element, point) pairs of a
-// tile (FP64 det F, F^-1, ln det F for Neo-Hookean; s mu_q, s lam_q for
-// elasticity) is computed up front by all threads, and the G/D phase of point
-// q + 1 runs together with the accumulation of point q (G is double-buffered),
-// so each point costs two barriers.
+//   G_a = J^-T grad Phi_a(X_q),   Y_a = Fi^T G_a                      (per e, q, a)
+//   A_e[(a,c)][(b,d)] += s_q ( mu d_cd (G_a . G_b) + alpha Y_a[d] Y_b[c] + lam Y_a[c] Y_b[d] )
+//
+// 24 FMA per (a, b) block of nine entries and point, and no per-point tangent
+// or left-operand tables.  Each thread owns one test function a and up to five
+// trial functions b of one element (45 accumulators); per point it reads
+// (G_a, Y_a) once and (G_b, Y_b) per b, two 16-byte shared loads each.  The
+// FP64 work (Neo-Hookean det F, F^-1 and ln det F) for every (element, point)
+// of a tile is done up front by all threads; the (G, Y) rows of point q + 1 are
+// formed while point q accumulates (double buffer): one barrier per point.
 #pragma once
 #include "common.cuh"
 
@@ -30,19 +33,30 @@ struct SeVecTile {
   static constexpr int NB = (NS + BB - 1) / BB;      // b-chunks per element
   static constexpr int TPE = NS * NB;                // threads per element
   static constexpr int GEO = 12;                     // Jinv[9], |det|
-  static constexpr int PW = 12;                      // pointwise record per (e, q)
-  static constexpr int LK = 12;                      // L_(a,c) row: 9 values (d, J) + pad
-  static constexpr int DP = 84;                      // D: 81 + pad
+  static constexpr int PW = 12;                      // per (e, q): Fi[9] (Neo-Hookean), s mu, s alpha, s lam
+  static constexpr int GY = 8;                       // per (e, a): G[3], pad, Y[3], pad
 
   FEA_HD static int max_tile() { return NT / TPE; }
   FEA_HD static size_t off_c(int TE) { return round_up_sz((size_t)TE * 12 * 8, 16); }
   FEA_HD static size_t off_geo(int TE) { return off_c(TE) + round_up_sz((size_t)TE * CLEN * 8, 16); }
   FEA_HD static size_t off_pw(int TE) { return off_geo(TE) + round_up_sz((size_t)TE * GEO * sizeof(T), 16); }
-  FEA_HD static size_t off_g(int TE, int Q) { return off_pw(TE) + round_up_sz((size_t)TE * Q * PW * sizeof(T), 16); }
-  FEA_HD static size_t off_d(int TE, int Q) { return off_g(TE, Q) + round_up_sz((size_t)2 * TE * NS * 4 * sizeof(T), 16); }
-  FEA_HD static size_t off_l(int TE, int Q) { return off_d(TE, Q) + round_up_sz((size_t)TE * DP * sizeof(T), 16); }
-  FEA_HD static size_t off_stage(int TE, int Q) { return off_l(TE, Q) + round_up_sz((size_t)TE * NS * 3 * LK * sizeof(T), 16); }
+  FEA_HD static size_t off_gy(int TE, int Q) { return off_pw(TE) + round_up_sz((size_t)TE * Q * PW * sizeof(T), 16); }
+  FEA_HD static size_t off_stage(int TE, int Q) { return off_gy(TE, Q) + round_up_sz((size_t)2 * TE * NS * GY * sizeof(T), 16); }
   FEA_HD static size_t smem(int TE, int Q) { return off_stage(TE, Q) + round_up_sz((size_t)TE * NN * sizeof(T), 16); }
+
+  template <int K>
+  __device__ static __forceinline__ void ld(const T* p, T (&v)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; k += 16 / (int)sizeof(T)) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p + k);
+        v[k] = x.x; v[k + 1] = x.y; v[k + 2] = x.z; v[k + 3] = x.w;
+      } else {
+        const double2 x = *reinterpret_cast<const double2*>(p + k);
+        v[k] = x.x; v[k + 1] = x.y;
+      }
+    }
+  }
 
   __device__ static void tile(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
     const int TE = q.tile, Q = q.Q;
@@ -50,9 +64,7 @@ struct SeVecTile {
     double* cs = reinterpret_cast<double*>(sm + off_c(TE));
     T* geo = reinterpret_cast<T*>(sm + off_geo(TE));
     T* PWs = reinterpret_cast<T*>(sm + off_pw(TE));
-    T* Gs = reinterpret_cast<T*>(sm + off_g(TE, Q));       // [2][TE][NS][4]
-    T* D = reinterpret_cast<T*>(sm + off_d(TE, Q));        // [TE][DP]
-    T* Lv = reinterpret_cast<T*>(sm + off_l(TE, Q));       // [TE][NS][3][LK]
+    T* GYs = reinterpret_cast<T*>(sm + off_gy(TE, Q));      // [2][TE][NS][GY]
     T* stage = reinterpret_cast<T*>(sm + off_stage(TE, Q));
     const TabLayout L = tab_layout(Q, NS, 0);
     const T* tab = reinterpret_cast<const T*>(q.tab);
@@ -100,9 +112,9 @@ struct SeVecTile {
           mu = fma(from_double<T>(cs[CLEN * e + k]), phi1[qq * 4 + k], mu);
           lam = fma(from_double<T>(cs[CLEN * e + 4 + k]), phi1[qq * 4 + k], lam);
         }
-        o[0] = s * mu;
-        o[1] = s * lam;
-        o[11] = s;
+        o[9] = s * mu;
+        o[10] = s * mu;
+        o[11] = s * lam;
       } else {
         const double* u = cs + CLEN * e;
         T gu[9];
@@ -142,54 +154,38 @@ struct SeVecTile {
         if (bad) flag_error(err, ERR_DEGENERATE);
         const double idF = 1.0 / dF;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) o[k] = bad ? nan : from_double<T>(cof[k] * idF);
-        o[9] = bad ? nan : from_double<T>(log(dF));
-        o[11] = s;
+        for (int k = 0; k < 9; ++k) o[k] = bad ? nan : from_double<T>(cof[k] * idF);  // o[3 i + j] = Fi[i][j]
+        const T lnJ = bad ? nan : from_double<T>(log(dF));
+        o[9] = s * mu_c;
+        o[10] = s * (mu_c - lam_c * lnJ);
+        o[11] = s * lam_c;
       }
     }
     __syncthreads();
 
-    // phase A of point qq: G into buffer qq & 1, and D
-    auto phase_a = [&](int qq) {
-      T* Gb = Gs + (size_t)(qq & 1) * TE * NS * 4;
+    // (G_a, Y_a) of point qq for every (element, a) into buffer qq & 1
+    auto rows = [&](int qq) {
+      T* Gb = GYs + (size_t)(qq & 1) * TE * NS * GY;
       for (int w = tid; w < ne * NS; w += NT) {
         const int e = w / NS, a = w - e * NS;
         const T* Ji = geo + GEO * e;
         const T* dp = dphi + (qq * NS + a) * 3;
-        T* o = Gb + 4 * w;
+        T G[3];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) o[x] = Ji[x] * dp[0] + Ji[3 + x] * dp[1] + Ji[6 + x] * dp[2];
-        o[3] = T(0);
-      }
-      for (int w = tid; w < ne * 81; w += NT) {
-        const int e = w / 81, k = w - e * 81;
-        const int c = k / 27, I = (k / 9) % 3, d = (k / 3) % 3, J = k % 3;
-        const T* pw = PWs + PW * (e * Q + qq);
-        T v;
-        if constexpr (FORM == 2) {
-          v = pw[0] * (T((c == d) && (I == J)) + T((I == d) && (c == J))) + pw[1] * T((c == I) && (d == J));
+        for (int x = 0; x < 3; ++x) G[x] = Ji[x] * dp[0] + Ji[3 + x] * dp[1] + Ji[6 + x] * dp[2];
+        T* o = Gb + GY * w;
+        o[0] = G[0]; o[1] = G[1]; o[2] = G[2]; o[3] = T(0);
+        if constexpr (FORM == 3) {
+          const T* fi = PWs + PW * (e * Q + qq);
+#pragma unroll
+          for (int x = 0; x < 3; ++x) o[4 + x] = G[0] * fi[x] + G[1] * fi[3 + x] + G[2] * fi[6 + x];
         } else {
-          v = pw[11] * (mu_c * T((c == d) && (I == J)) + (mu_c - lam_c * pw[9]) * pw[3 * J + c] * pw[3 * I + d] +
-                        lam_c * pw[3 * I + c] * pw[3 * J + d]);
+          o[4] = G[0]; o[5] = G[1]; o[6] = G[2];
         }
-        D[e * DP + k] = v;
-      }
-    };
-    // phase B of point qq: left operands L_(a,c)[d,J]
-    auto phase_b = [&](int qq) {
-      const T* Gb = Gs + (size_t)(qq & 1) * TE * NS * 4;
-      for (int w = tid; w < ne * NS * 9; w += NT) {
-        const int e = w / (NS * 9), rem = w - e * NS * 9, a = rem / 9, cd = rem % 9, c = cd / 3, d = cd % 3;
-        const T* g = Gb + 4 * (e * NS + a);
-        const T* Dp = D + e * DP + c * 27 + d * 3;
-        T* o = Lv + (size_t)((e * NS + a) * 3 + c) * LK + 3 * d;
-        const T g0 = g[0], g1 = g[1], g2 = g[2];
-#pragma unroll
-        for (int J = 0; J < 3; ++J) o[J] = g0 * Dp[J] + g1 * Dp[9 + J] + g2 * Dp[18 + J];
+        o[7] = T(0);
       }
     };
 
-    // this thread's block: element e, test function a, trial functions b0 .. b0 + nb - 1
     const int te = tid / TPE, r = tid - te * TPE;
     const int a = r / NB, b0 = (r - a * NB) * BB;
     const int nb = NS - b0 < BB ? NS - b0 : BB;
@@ -200,38 +196,35 @@ struct SeVecTile {
 #pragma unroll
       for (int k = 0; k < 9; ++k) acc[i][k] = T(0);
 
-    phase_a(0);
-    __syncthreads();
-    phase_b(0);
+    rows(0);
     __syncthreads();
     for (int qq = 0; qq < Q; ++qq) {
       if (owner) {
-        const T* Gb = Gs + (size_t)(qq & 1) * TE * NS * 4 + (size_t)(te * NS + b0) * 4;
-        const T* lv = Lv + (size_t)(te * NS + a) * 3 * LK;
-        T l[27];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int k = 0; k < 9; ++k) l[9 * c + k] = lv[c * LK + k];
+        const T* Gb = GYs + (size_t)(qq & 1) * TE * NS * GY + (size_t)te * NS * GY;
+        const T* pw = PWs + PW * (te * Q + qq);
+        const T smu = pw[9], sal = pw[10], slam = pw[11];
+        T ga[8];
+        ld<8>(Gb + GY * a, ga);
+        // scaled test rows: alpha Y_a and lam Y_a
+        const T ay0 = sal * ga[4], ay1 = sal * ga[5], ay2 = sal * ga[6];
+        const T ly0 = slam * ga[4], ly1 = slam * ga[5], ly2 = slam * ga[6];
+        const T ay[3] = {ay0, ay1, ay2}, ly[3] = {ly0, ly1, ly2};
 #pragma unroll
         for (int i = 0; i < BB; ++i) {
           if (i < nb) {
-            const T g0 = Gb[4 * i], g1 = Gb[4 * i + 1], g2 = Gb[4 * i + 2];
+            T gb[8];
+            ld<8>(Gb + GY * (b0 + i), gb);
+            const T dot = smu * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
               for (int d = 0; d < 3; ++d)
-                acc[i][3 * c + d] =
-                    fma(l[9 * c + 3 * d], g0, fma(l[9 * c + 3 * d + 1], g1, fma(l[9 * c + 3 * d + 2], g2, acc[i][3 * c + d])));
+                acc[i][3 * c + d] = fma(ay[d], gb[4 + c], fma(ly[c], gb[4 + d], acc[i][3 * c + d] + (c == d ? dot : T(0))));
           }
         }
       }
-      if (qq + 1 < Q) phase_a(qq + 1);  // other G buffer; D was consumed by phase_b(qq)
+      if (qq + 1 < Q) rows(qq + 1);  // the other buffer, last read at point qq - 1
       __syncthreads();
-      if (qq + 1 < Q) {
-        phase_b(qq + 1);  // Lv of point qq was consumed by the accumulation above
-        __syncthreads();
-      }
     }
     if (owner) {
       T* o = stage + (size_t)te * NN + (3 * a) * N + 3 * b0;

@@ -44,19 +44,34 @@ def candidates(form, p, precision=fea.PREC_FP32):
     return out
 
 
+HBM_GBS = 6753.8           # measured copy bandwidth of the GB300s
+FP32_TFLOPS = 80.5         # 152 SMs x 128 lanes x 2 x 2.07 GHz
+FP64_TFLOPS = 1.26         # 152 SMs x 2 lanes x 2 x 2.07 GHz
+
+
 def features(form, p, variant, tile, precision=fea.PREC_FP32):
-    """Loop-nest features of one candidate (fixed scaling, D_IN values)."""
+    """Loop-nest features of one candidate (fixed scaling, D_IN values): the
+    roofline times its operation and byte counts predict, the tile and the
+    occupancy its shared memory allows, and what the loop nest is."""
     pl = fea.plan(form, p, precision=precision, variant=variant, tile=tile)
     ns = (p + 1) * (p + 2) * (p + 3) // 6
-    onehot = [1.0 if form == k else 0.0 for k in range(4)]
+    fp64 = 30 + (70 * pl["quad_points"] if form == fea.NEOHOOKEAN else 0)
+    t_mem = pl["bytes"] / (HBM_GBS * 1e9)
+    t_f32 = pl["flops_run"] / (FP32_TFLOPS * 1e12)
+    t_f64 = fp64 / (FP64_TFLOPS * 1e12)
+    ctas = max(1, min(8, 232448 // max(pl["smem_bytes"], 1)))
     return [ns / 35.0,
             math.log2(pl["quad_points"]) / 9.0,
             1.0 if form in (fea.ELASTICITY, fea.NEOHOOKEAN) else 0.0,
             1.0 if variant == fea.VARIANT_PRE else 0.0,
             math.log2(tile) / 8.0,
-            math.log2(max(pl["flops_run"], 1)) / 24.0,
-            math.log2(pl["bytes"]) / 18.0,
-            pl["smem_bytes"] / 232448.0] + onehot
+            (math.log2(t_mem) + 30.0) / 10.0,
+            (math.log2(max(t_f32, 1e-15)) + 30.0) / 10.0,
+            (math.log2(t_f64) + 30.0) / 10.0,
+            ctas / 8.0,
+            math.log2(max(t_mem, t_f32, t_f64) * 1e9) / 10.0,
+            1.0 if form == fea.NEOHOOKEAN else 0.0,
+            1.0 if form == fea.MASS else 0.0]
 
 
 def _inputs(form, p, E, seed):
@@ -161,11 +176,19 @@ def train(records, epochs=3000, lr=1e-2, hidden=HIDDEN, seed=0):
     return model
 
 
+MARGIN = 0.15  # log2 units: switch away from the flop-count choice only for a predicted gain above ~11%
+
+
 def choose(model, form, p, precision=fea.PREC_FP32, install=True):
-    """The candidate the model predicts fastest; installed for AUTO calls."""
+    """The candidate the model predicts fastest, installed for AUTO calls.  The
+    paper's flop-count choice stays unless the model predicts a clear gain."""
     cands = candidates(form, p, precision)
     pred = model.predict([features(form, p, v, t, precision) for v, t in cands])
-    v, t = cands[int(np.argmin(pred))]
+    fallback = flop_choice(form, p, precision)
+    best = int(np.argmin(pred))
+    v, t = cands[best]
+    if fallback in cands and pred[cands.index(fallback)] - pred[best] < MARGIN:
+        v, t = fallback
     if install:
         fea.tune_set(form, p, variant=v, tile=t, precision=precision)
     return v, t
@@ -173,8 +196,7 @@ def choose(model, form, p, precision=fea.PREC_FP32, install=True):
 
 def flop_choice(form, p, precision=fea.PREC_FP32):
     """The paper's choice: Algorithm 3's variant with the default tile."""
-    fea.tune_clear()
-    pl = fea.plan(form, p, precision=precision)
+    pl = fea.plan_flop(form, p, precision=precision)
     return pl["variant"], pl["tile"]
 
 

@@ -48,7 +48,7 @@ def test_tune_set_changes_auto_plan_and_clear_restores():
 def test_tuned_choice_is_correct_and_mlp_gains(fea, orc, tmp_path):
     import torch
     from paper_1604_05872_gb300 import inputs, tuning
-    configs = [(1, 2), (1, 3), (2, 2), (2, 3), (3, 2), (0, 3)]
+    configs = [(0, 2), (0, 3), (1, 2), (1, 3), (1, 4), (2, 2), (2, 3), (3, 1), (3, 2), (3, 3)]
     records = tuning.autotune(configs, reps=3)
     assert len(records) >= 4 * len(configs)
     gains, regrets = [], []
