@@ -193,7 +193,7 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
   int TE = o.tile;
   if (TE < 0) return fail(FEA_EINVAL, "negative tile");
   // tuned tiles were measured on the standalone kernels; the batch keeps its own rule
-  if (TE == 0) TE = default_tile(variant, form, p, prec, k->max_tile, budget, Q, k->smem, use_tuned && !batch);
+  if (TE == 0) TE = default_tile(variant, form, p, prec, k->max_tile, budget, Q, k->smem, use_tuned && !batch, k->pref_tile);
   if (TE < 1 || TE > k->max_tile) return fail(FEA_EINVAL, "tile out of range for this kernel");
   const size_t smem = k->smem(TE, Q);
   if (smem > budget) return fail(FEA_EINVAL, "tile does not fit the shared-memory budget (Constraint 2)");

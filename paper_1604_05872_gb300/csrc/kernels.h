@@ -11,6 +11,7 @@ struct KernelInfo {
   int variant, form, p, prec;         // prec: 0 = FP64, 1 = FP32
   int max_tile;                       // upper bound on elements per tile
   size_t (*smem)(int TE, int Q);      // dynamic shared memory for a tile of TE
+  int pref_tile;                      // tile the thread layout is built for (0: none)
 };
 
 // Registered by the kernel translation units.

@@ -10,7 +10,7 @@ template <int F, int P>
 size_t stream_smem(int TE, int Q) { return PreStream<F, P>::smem(TE, Q); }
 template <int F, int P>
 KernelInfo stream_info() {
-  return KernelInfo{reinterpret_cast<const void*>(&pre_stream_kernel<F, P>), V_PRE, F, P, 1, NT, &stream_smem<F, P>};
+  return KernelInfo{reinterpret_cast<const void*>(&pre_stream_kernel<F, P>), V_PRE, F, P, 1, NT, &stream_smem<F, P>, 0};
 }
 
 #define PRE(F, P) make_info<PreTile<F, P, float>>(V_PRE, F, P, 1), make_info<PreTile<F, P, double>>(V_PRE, F, P, 0)

@@ -3,6 +3,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <type_traits>
+
 namespace fea {
 
 __device__ __forceinline__ unsigned dynamic_smem_bytes() {
@@ -32,9 +34,17 @@ __global__ void __launch_bounds__(NT) run_tiles(Req q, unsigned* err) {
 template <class K>
 size_t smem_of(int TE, int Q) { return K::smem(TE, Q); }
 
+// Tile functions whose thread layout is built for a given tile say so with
+// pref_tile(); the others take the planner's shared-memory rule.
+template <class K, class = void>
+struct PrefTile { static int get() { return 0; } };
+template <class K>
+struct PrefTile<K, std::void_t<decltype(K::pref_tile())>> { static int get() { return K::pref_tile(); } };
+
 template <class K>
 KernelInfo make_info(int variant, int form, int p, int prec) {
-  return KernelInfo{reinterpret_cast<const void*>(&run_tiles<K>), variant, form, p, prec, K::max_tile(), &smem_of<K>};
+  return KernelInfo{reinterpret_cast<const void*>(&run_tiles<K>), variant, form, p, prec, K::max_tile(), &smem_of<K>,
+                    PrefTile<K>::get()};
 }
 
 }  // namespace fea

@@ -177,9 +177,14 @@ int choose_variant(int form, int p, int prec, size_t budget, bool use_tuned) {
 }
 
 int default_tile(int variant, int form, int p, int prec, int max_tile, size_t budget, int Q,
-                 size_t (*smem)(int, int), bool use_tuned) {
+                 size_t (*smem)(int, int), bool use_tuned, int pref_tile) {
   int v = 0, t = 0;
   if (use_tuned && get_tuned(form, p, prec, &v, &t) && t > 0 && t <= max_tile && smem(t, Q) <= budget) return t;
+  if (pref_tile > 0) {  // the kernel's thread layout is built for this tile
+    int te = std::min(pref_tile, max_tile);
+    while (te > 1 && smem(te, Q) > budget) --te;
+    return te;
+  }
   // target a few resident CTAs per SM: about 48 KB of shared memory per tile
   const size_t target = std::min<size_t>(budget, 48 * 1024);
   int best = 1;

@@ -28,7 +28,7 @@ OpCounts op_counts(int form, int p);
 // Tuned choices installed with set_tuned() take precedence.
 int choose_variant(int form, int p, int prec, size_t budget, bool use_tuned = true);
 int default_tile(int variant, int form, int p, int prec, int max_tile, size_t budget, int Q,
-                 size_t (*smem)(int, int), bool use_tuned = true);
+                 size_t (*smem)(int, int), bool use_tuned = true, int pref_tile = 0);
 
 // Tuned overrides (autotuner / learned cost model), keyed by (form, p, prec).
 void set_tuned(int form, int p, int prec, int variant, int tile);

@@ -13,12 +13,15 @@
 //   A_e[(a,.)][(b,.)] = ( tr(M X) I + adj^T (X^T + L) adj ) / |det J|
 //
 // 144 FMA per (a, b) block instead of 324 for the plain geometry-tensor GEMV.
+// The tangent is symmetric (block (b, a) is the transpose of block (a, b)), so
+// only blocks a <= b are evaluated and each is written twice (sym.cuh).
 // Each thread owns one (a, b) pair, keeps its 36 R values in registers and
 // sweeps the tile's elements, reading the element's adjugate, M and
 // coefficients with broadcast shared loads; results are staged in shared memory
 // and written with coalesced 16-byte stores.
 #pragma once
 #include "common.cuh"
+#include "sym.cuh"
 
 namespace fea {
 
@@ -28,7 +31,8 @@ struct PreVecTile {
   static constexpr int NS = nbasis_c(P);
   static constexpr int N = 3 * NS;
   static constexpr int NN = N * N;
-  static constexpr int S = NS * NS;              // (a, b) slots
+  static constexpr int S = NS * NS;              // (a, b) slots of the table
+  static constexpr int NP = NS * (NS + 1) / 2;   // evaluated pairs a <= b
   static constexpr int CLEN = 8;
   static constexpr int GEO = 32;                 // adj[9], M[9], mu[4], lam[4], 1/|det|, pad
 
@@ -72,8 +76,10 @@ struct PreVecTile {
     }
     __syncthreads();
 
-    for (int s = tid; s < S; s += NT) {
-      const int a = s / NS, b = s - a * NS;
+    for (int k = tid; k < NP; k += NT) {
+      const unsigned ab = kSymPairs<NS>.c[k];
+      const int a = (int)(ab & 0xffu), b = (int)(ab >> 8);
+      const int s = a * NS + b;
       T R[36];
 #pragma unroll
       for (int r = 0; r < 36; ++r) R[r] = __ldg(Rg + (size_t)r * S + s);
@@ -100,16 +106,17 @@ struct PreVecTile {
             Pm[3 * al + d] = v;
           }
         const T inv = g[26];
-        T* o = stage + (size_t)e * NN + (3 * a) * N + 3 * b;
+        T v[9];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            T v = c == d ? tr : T(0);
+            T x = c == d ? tr : T(0);
 #pragma unroll
-            for (int al = 0; al < 3; ++al) v = fma(g[3 * al + c], Pm[3 * al + d], v);
-            o[c * N + d] = v * inv;
+            for (int al = 0; al < 3; ++al) x = fma(g[3 * al + c], Pm[3 * al + d], x);
+            v[3 * c + d] = x * inv;
           }
+        put_sym_block<N, T>(stage + (size_t)e * NN, a, b, v);
       }
     }
     __syncthreads();

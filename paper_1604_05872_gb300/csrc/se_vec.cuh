@@ -1,71 +1,84 @@
 // Sharing-elimination variant for the vector forms (elasticity, Neo-Hookean).
 //
 // Both tangents have the structure
-//   A[c,I][d,J] = mu d_cd d_IJ + alpha Fi_Jc Fi_Id + lam Fi_Ic Fi_Jd
-// (Neo-Hookean: Fi = F^-1, alpha = mu - lam ln det F, mu and lam constants;
-// elasticity: Fi = I, alpha = mu, with mu, lam the P1 fields at the point).
-// Factorising the test/trial contraction through it (Section 3.2: expansion,
-// factorisation and code motion of what depends on (e, q) or (e, q, a) only):
+//   A[(a,c)][(b,d)] = sum_q s_q ( mu d_cd G_a.G_b + alpha Y_a[d] Y_b[c] + lam Y_a[c] Y_b[d] )
+// with G_a = J^-T grad Phi_a(X_q) and
+//   elasticity:   Y = G,           alpha = mu,  mu and lam the P1 fields at the point;
+//   Neo-Hookean:  Y = F^-T G,      alpha = mu - lam ln det F, mu and lam constants.
+// Factorising the test/trial contraction through this structure (Section 3.2:
+// expansion, factorisation and code motion of what depends on (e, q) or
+// (e, q, a) only) leaves, per block (a, b), three accumulations over the points:
 //
-//   G_a = J^-T grad Phi_a(X_q),   Y_a = Fi^T G_a                      (per e, q, a)
-//   A_e[(a,c)][(b,d)] += s_q ( mu d_cd (G_a . G_b) + alpha Y_a[d] Y_b[c] + lam Y_a[c] Y_b[d] )
+//   W1 = sum_q s alpha Y_a (x) Y_b,   W2 = sum_q s lam Y_a (x) Y_b,   D = sum_q s mu G_a.G_b
+//   A[(a,.)][(b,.)] = D I + W1^T + W2
 //
-// 24 FMA per (a, b) block of nine entries and point, and no per-point tangent
-// or left-operand tables.  Each thread owns one test function a and up to five
-// trial functions b of one element (45 accumulators); per point it reads
-// (G_a, Y_a) once and (G_b, Y_b) per b, two 16-byte shared loads each.  The
-// FP64 work (Neo-Hookean det F, F^-1 and ln det F) for every (element, point)
-// of a tile is done up front by all threads; the (G, Y) rows of point q + 1 are
-// formed while point q accumulates (double buffer): one barrier per point.
+// For elasticity D = tr W1.  For Neo-Hookean D = Z_a . Y_b with Z_a = s mu F G_a
+// (since G_b = F^T Y_b).  The tangents are symmetric, so only blocks a <= b are
+// accumulated (runs of up to BB trial functions per thread, see sym.cuh) and
+// each is written as itself and transposed.
+//
+// Per block and point: one 16-byte shared load of Y_b = (Y0, Y1, Y2, Y2) and
+// ten (elasticity) or twelve (Neo-Hookean) packed/scalar FMAs; the a-side
+// factors (s alpha Y_a, s lam Y_a, Z_a) sit in registers for the whole run.
+//
+// Thread layout: EF consecutive lanes take EF elements of the tile with the same
+// run, so a warp holds 32 / EF runs of (nearly) equal length and reads the rows
+// of EF elements at once (element rows are an odd number of 16-byte slots
+// apart: conflict-free).  Pointwise data (Neo-Hookean: F, F^-1, ln det F, in
+// the tile's precision) are computed for every (element, point) up front; the
+// (Y, Z) rows of the next QG points are formed while the current QG points
+// accumulate (double buffer, one barrier per QG points).
 #pragma once
 #include "common.cuh"
+#include "sym.cuh"
 
 namespace fea {
 
 template <int FORM, int P, typename T>
 struct SeVecTile {
   static_assert(FORM == 2 || FORM == 3, "vector forms");
+  static constexpr bool NEO = FORM == 3;
+  static constexpr bool F32 = sizeof(T) == 4;
   static constexpr int NS = nbasis_c(P);
   static constexpr int N = 3 * NS;
   static constexpr int NN = N * N;
   static constexpr int CLEN = coeff_len_c(FORM, P);
-  static constexpr int BB = 5;                       // trial functions per thread
-  static constexpr int NB = (NS + BB - 1) / BB;      // b-chunks per element
-  static constexpr int TPE = NS * NB;                // threads per element
-  static constexpr int GEO = 12;                     // Jinv[9], |det|
-  static constexpr int PW = 12;                      // per (e, q): Fi[9] (Neo-Hookean), s mu, s alpha, s lam
-  static constexpr int GY = 8;                       // per (e, a): G[3], pad, Y[3], pad
+  // trial functions per thread and elements interleaved per warp
+  static constexpr int BB = F32 ? (P == 1 ? 2 : P == 4 ? 3 : 4) : (P == 4 ? 3 : 2);
+  static constexpr int EF = P == 1 ? 8 : P == 2 ? (F32 ? 4 : 8) : P == 3 ? (F32 ? 4 : 2) : 1;
+  using Chunks = SymChunks<NS, BB>;
+  static constexpr int NCH = Chunks::NCH;
+  static constexpr int GROUPS = NT / (EF * NCH);
+  static_assert(GROUPS >= 1, "one element group must fit the CTA");
+  static constexpr int TEMAX = EF * GROUPS;
+  static constexpr int NSP = NS | 1;                 // row slots per element (odd)
+  static constexpr int QG = 3;                       // points per barrier
+  static constexpr int GEO = 12;                     // Jinv[9], |det|, pad
+  static constexpr int PW = NEO ? 20 : 4;            // per (e, q): [Fi[9], s mu F[9],] s alpha, s lam
+  static constexpr int RW = NEO ? 2 : 1;             // 16-byte rows per (e, a): Y [, Z]
+  using V2 = typename Vec2Of<T>::type;
 
-  FEA_HD static int max_tile() { return NT / TPE; }
+  FEA_HD static int max_tile() { return TEMAX; }
+  FEA_HD static int pref_tile() { return TEMAX; }
   FEA_HD static size_t off_c(int TE) { return round_up_sz((size_t)TE * 12 * 8, 16); }
-  FEA_HD static size_t off_geo(int TE) { return off_c(TE) + round_up_sz((size_t)TE * CLEN * 8, 16); }
+  FEA_HD static size_t off_ct(int TE) { return off_c(TE) + round_up_sz((size_t)TE * CLEN * 8, 16); }
+  FEA_HD static size_t off_geo(int TE) { return off_ct(TE) + round_up_sz((size_t)TE * CLEN * sizeof(T), 16); }
   FEA_HD static size_t off_pw(int TE) { return off_geo(TE) + round_up_sz((size_t)TE * GEO * sizeof(T), 16); }
-  FEA_HD static size_t off_gy(int TE, int Q) { return off_pw(TE) + round_up_sz((size_t)TE * Q * PW * sizeof(T), 16); }
-  FEA_HD static size_t off_stage(int TE, int Q) { return off_gy(TE, Q) + round_up_sz((size_t)2 * TE * NS * GY * sizeof(T), 16); }
+  FEA_HD static size_t off_rows(int TE, int Q) { return off_pw(TE) + round_up_sz((size_t)TE * Q * PW * sizeof(T), 16); }
+  FEA_HD static size_t rows_len(int TE) { return (size_t)QG * TE * NSP * 4; }  // T per buffer and row kind
+  FEA_HD static size_t off_stage(int TE, int Q) { return off_rows(TE, Q) + (size_t)2 * RW * rows_len(TE) * sizeof(T); }
   FEA_HD static size_t smem(int TE, int Q) { return off_stage(TE, Q) + round_up_sz((size_t)TE * NN * sizeof(T), 16); }
-
-  template <int K>
-  __device__ static __forceinline__ void ld(const T* p, T (&v)[K]) {
-#pragma unroll
-    for (int k = 0; k < K; k += 16 / (int)sizeof(T)) {
-      if constexpr (sizeof(T) == 4) {
-        const float4 x = *reinterpret_cast<const float4*>(p + k);
-        v[k] = x.x; v[k + 1] = x.y; v[k + 2] = x.z; v[k + 3] = x.w;
-      } else {
-        const double2 x = *reinterpret_cast<const double2*>(p + k);
-        v[k] = x.x; v[k + 1] = x.y;
-      }
-    }
-  }
 
   __device__ static void tile(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
     const int TE = q.tile, Q = q.Q;
     double* xs = reinterpret_cast<double*>(sm);
     double* cs = reinterpret_cast<double*>(sm + off_c(TE));
+    T* ct = reinterpret_cast<T*>(sm + off_ct(TE));
     T* geo = reinterpret_cast<T*>(sm + off_geo(TE));
     T* PWs = reinterpret_cast<T*>(sm + off_pw(TE));
-    T* GYs = reinterpret_cast<T*>(sm + off_gy(TE, Q));      // [2][TE][NS][GY]
+    T* rows = reinterpret_cast<T*>(sm + off_rows(TE, Q));   // [2][RW][QG][TE][NSP][4]
     T* stage = reinterpret_cast<T*>(sm + off_stage(TE, Q));
+    const size_t RL = rows_len(TE);
     const TabLayout L = tab_layout(Q, NS, 0);
     const T* tab = reinterpret_cast<const T*>(q.tab);
     const T* Wt = tab + L.offW;
@@ -83,7 +96,7 @@ struct SeVecTile {
       const bool bad = !(fabs(det) > 0.0) || !isfinite(det);
       if (bad) flag_error(err, ERR_DEGENERATE);
       T* g = geo + GEO * tid;
-      if constexpr (sizeof(T) == 4) {
+      if constexpr (F32) {
         const float df = d2f(det), inv = 1.0f / df;
 #pragma unroll
         for (int k = 0; k < 9; ++k) g[k] = bad ? nan : d2f(adj[k]) * inv;
@@ -95,9 +108,10 @@ struct SeVecTile {
         g[9] = bad ? nan : fabs(det);
       }
     }
+    for (int k = tid; k < ne * CLEN; k += NT) ct[k] = from_double<T>(cs[k]);
     __syncthreads();
-    const T mu_c = FORM == 3 ? from_double<T>(q.coeffs[q.E * CLEN]) : T(0);
-    const T lam_c = FORM == 3 ? from_double<T>(q.coeffs[q.E * CLEN + 1]) : T(0);
+    const T mu_c = NEO ? from_double<T>(q.coeffs[q.E * CLEN]) : T(0);
+    const T lam_c = NEO ? from_double<T>(q.coeffs[q.E * CLEN + 1]) : T(0);
 
     // pointwise data of every (element, point) of the tile
     for (int w = tid; w < ne * Q; w += NT) {
@@ -105,136 +119,192 @@ struct SeVecTile {
       const T* Ji = geo + GEO * e;
       T* o = PWs + PW * w;
       const T s = Wt[qq] * Ji[9];
-      if constexpr (FORM == 2) {
+      if constexpr (!NEO) {
         T mu = T(0), lam = T(0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          mu = fma(from_double<T>(cs[CLEN * e + k]), phi1[qq * 4 + k], mu);
-          lam = fma(from_double<T>(cs[CLEN * e + 4 + k]), phi1[qq * 4 + k], lam);
+          mu = fma(ct[CLEN * e + k], phi1[qq * 4 + k], mu);
+          lam = fma(ct[CLEN * e + 4 + k], phi1[qq * 4 + k], lam);
         }
-        o[9] = s * mu;
-        o[10] = s * mu;
-        o[11] = s * lam;
+        o[PW - 2] = s * mu;   // alpha = mu
+        o[PW - 1] = s * lam;
       } else {
-        const double* u = cs + CLEN * e;
-        T gu[9];
+        // grad u = (sum_a u_a (x) grad_X Phi_a) J^-1
+        const T* u = ct + CLEN * e;
+        T gr[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) gu[k] = T(0);
+        for (int k = 0; k < 9; ++k) gr[k] = T(0);
         for (int a = 0; a < NS; ++a) {
           const T* dp = dphi + (qq * NS + a) * 3;
-          T G[3];
-#pragma unroll
-          for (int x = 0; x < 3; ++x) G[x] = Ji[x] * dp[0] + Ji[3 + x] * dp[1] + Ji[6 + x] * dp[2];
+          const T d0 = dp[0], d1 = dp[1], d2 = dp[2];
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            const T ui = from_double<T>(u[3 * a + i]);
-#pragma unroll
-            for (int x = 0; x < 3; ++x) gu[3 * i + x] = fma(ui, G[x], gu[3 * i + x]);
+            const T ui = u[3 * a + i];
+            gr[3 * i] = fma(ui, d0, gr[3 * i]);
+            gr[3 * i + 1] = fma(ui, d1, gr[3 * i + 1]);
+            gr[3 * i + 2] = fma(ui, d2, gr[3 * i + 2]);
           }
         }
-        double F[9];
+        T F[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            F[3 * i + x] = (i == x ? T(1) : T(0)) + gr[3 * i] * Ji[x] + gr[3 * i + 1] * Ji[3 + x] + gr[3 * i + 2] * Ji[6 + x];
+        T cof[9];  // det(F) F^-1
+        cof[0] = F[4] * F[8] - F[5] * F[7];
+        cof[1] = F[2] * F[7] - F[1] * F[8];
+        cof[2] = F[1] * F[5] - F[2] * F[4];
+        cof[3] = F[5] * F[6] - F[3] * F[8];
+        cof[4] = F[0] * F[8] - F[2] * F[6];
+        cof[5] = F[2] * F[3] - F[0] * F[5];
+        cof[6] = F[3] * F[7] - F[4] * F[6];
+        cof[7] = F[1] * F[6] - F[0] * F[7];
+        cof[8] = F[0] * F[4] - F[1] * F[3];
+        const T dF = F[0] * cof[0] + F[1] * cof[3] + F[2] * cof[6];
+        const bool bad = !(dF > T(0)) || !isfinite(dF);
+        if (bad) flag_error(err, ERR_DEGENERATE);
+        const T idF = T(1) / dF;
+        T lnJ;
+        if constexpr (F32) lnJ = logf(dF);
+        else lnJ = log(dF);
+        const T smu = s * mu_c;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          if constexpr (sizeof(T) == 4) F[k] = f2d(gu[k]);
-          else F[k] = gu[k];
+          o[k] = bad ? nan : cof[k] * idF;  // o[3 i + j] = Fi[i][j]
+          o[9 + k] = bad ? nan : smu * F[k];
         }
-        F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
-        double cof[9];  // det(F) F^-1
-        cof[0] = fma(F[4], F[8], -F[5] * F[7]);
-        cof[1] = fma(F[2], F[7], -F[1] * F[8]);
-        cof[2] = fma(F[1], F[5], -F[2] * F[4]);
-        cof[3] = fma(F[5], F[6], -F[3] * F[8]);
-        cof[4] = fma(F[0], F[8], -F[2] * F[6]);
-        cof[5] = fma(F[2], F[3], -F[0] * F[5]);
-        cof[6] = fma(F[3], F[7], -F[4] * F[6]);
-        cof[7] = fma(F[1], F[6], -F[0] * F[7]);
-        cof[8] = fma(F[0], F[4], -F[1] * F[3]);
-        const double dF = fma(F[0], cof[0], fma(F[1], cof[3], F[2] * cof[6]));
-        const bool bad = !(dF > 0.0) || !isfinite(dF);
-        if (bad) flag_error(err, ERR_DEGENERATE);
-        const double idF = 1.0 / dF;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) o[k] = bad ? nan : from_double<T>(cof[k] * idF);  // o[3 i + j] = Fi[i][j]
-        const T lnJ = bad ? nan : from_double<T>(log(dF));
-        o[9] = s * mu_c;
-        o[10] = s * (mu_c - lam_c * lnJ);
-        o[11] = s * lam_c;
+        o[PW - 2] = bad ? nan : s * (mu_c - lam_c * lnJ);
+        o[PW - 1] = s * lam_c;
       }
     }
     __syncthreads();
 
-    // (G_a, Y_a) of point qq for every (element, a) into buffer qq & 1
-    auto rows = [&](int qq) {
-      T* Gb = GYs + (size_t)(qq & 1) * TE * NS * GY;
-      for (int w = tid; w < ne * NS; w += NT) {
-        const int e = w / NS, a = w - e * NS;
+    // rows of points [g QG, g QG + QG) into buffer g & 1: Y = (Y0, Y1, Y2, Y2), Z = (Z0, Z1, Z2, 0)
+    const int ngroups = (Q + QG - 1) / QG;
+    auto make_rows = [&](int g) {
+      T* Yb = rows + (size_t)(g & 1) * RW * RL;
+      const int q0 = g * QG;
+      const int nq = Q - q0 < QG ? Q - q0 : QG;
+      for (int w = tid; w < nq * ne * NS; w += NT) {
+        const int qi = w / (ne * NS), r = w - qi * (ne * NS);
+        const int e = r / NS, a = r - e * NS;
+        const int qq = q0 + qi;
         const T* Ji = geo + GEO * e;
         const T* dp = dphi + (qq * NS + a) * 3;
+        const T d0 = dp[0], d1 = dp[1], d2 = dp[2];
         T G[3];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) G[x] = Ji[x] * dp[0] + Ji[3 + x] * dp[1] + Ji[6 + x] * dp[2];
-        T* o = Gb + GY * w;
-        o[0] = G[0]; o[1] = G[1]; o[2] = G[2]; o[3] = T(0);
-        if constexpr (FORM == 3) {
-          const T* fi = PWs + PW * (e * Q + qq);
+        for (int x = 0; x < 3; ++x) G[x] = Ji[x] * d0 + Ji[3 + x] * d1 + Ji[6 + x] * d2;
+        const size_t slot = (((size_t)qi * TE + e) * NSP + a) * 4;
+        T Y[3];
+        if constexpr (NEO) {
+          const T* pw = PWs + PW * (e * Q + qq);
 #pragma unroll
-          for (int x = 0; x < 3; ++x) o[4 + x] = G[0] * fi[x] + G[1] * fi[3 + x] + G[2] * fi[6 + x];
+          for (int x = 0; x < 3; ++x) Y[x] = G[0] * pw[x] + G[1] * pw[3 + x] + G[2] * pw[6 + x];
+          T* z = Yb + RL + slot;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) z[i] = pw[9 + 3 * i] * G[0] + pw[10 + 3 * i] * G[1] + pw[11 + 3 * i] * G[2];
+          z[3] = T(0);
         } else {
-          o[4] = G[0]; o[5] = G[1]; o[6] = G[2];
+          Y[0] = G[0]; Y[1] = G[1]; Y[2] = G[2];
         }
-        o[7] = T(0);
+        T* y = Yb + slot;
+        y[0] = Y[0]; y[1] = Y[1]; y[2] = Y[2]; y[3] = Y[2];
       }
     };
 
-    const int te = tid / TPE, r = tid - te * TPE;
-    const int a = r / NB, b0 = (r - a * NB) * BB;
-    const int nb = NS - b0 < BB ? NS - b0 : BB;
-    const bool owner = te < ne;
-    T acc[BB][9];
-#pragma unroll
-    for (int i = 0; i < BB; ++i)
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc[i][k] = T(0);
+    // this thread's run of trial functions
+    const int el = tid % EF, slot = tid / EF;
+    const int grp = slot / NCH, ch = slot - grp * NCH;
+    const int te = grp * EF + el;
+    const bool owner = grp < GROUPS && te < ne;
+    const unsigned cw = owner ? kSymChunks<NS, BB>.c[ch] : 0u;
+    const int a = (int)(cw & 0xffu), b0 = (int)((cw >> 8) & 0xffu), nb = (int)(cw >> 16);
 
-    rows(0);
+    V2 w1r[BB][3], w2r[BB][3], w1c[BB], w2c[BB], dd[BB];
+    T w1s[BB], w2s[BB], ds[BB];
+#pragma unroll
+    for (int i = 0; i < BB; ++i) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w1r[i][c] = w2r[i][c] = vmk(T(0), T(0));
+      w1c[i] = w2c[i] = dd[i] = vmk(T(0), T(0));
+      w1s[i] = w2s[i] = ds[i] = T(0);
+    }
+
+    make_rows(0);
     __syncthreads();
-    for (int qq = 0; qq < Q; ++qq) {
+    for (int g = 0; g < ngroups; ++g) {
       if (owner) {
-        const T* Gb = GYs + (size_t)(qq & 1) * TE * NS * GY + (size_t)te * NS * GY;
-        const T* pw = PWs + PW * (te * Q + qq);
-        const T smu = pw[9], sal = pw[10], slam = pw[11];
-        T ga[8];
-        ld<8>(Gb + GY * a, ga);
-        // scaled test rows: alpha Y_a and lam Y_a
-        const T ay0 = sal * ga[4], ay1 = sal * ga[5], ay2 = sal * ga[6];
-        const T ly0 = slam * ga[4], ly1 = slam * ga[5], ly2 = slam * ga[6];
-        const T ay[3] = {ay0, ay1, ay2}, ly[3] = {ly0, ly1, ly2};
+        const T* Yb = rows + (size_t)(g & 1) * RW * RL;
+        const int q0 = g * QG;
+        const int nq = Q - q0 < QG ? Q - q0 : QG;
+        for (int qi = 0; qi < nq; ++qi) {
+          const T* yr = Yb + (((size_t)qi * TE + te) * NSP) * 4;
+          const T* pw = PWs + PW * (te * Q + q0 + qi);
+          const T sal = pw[PW - 2], slam = pw[PW - 1];
+          T y0, y1, y2, y3;
+          ld4(yr + 4 * a, y0, y1, y2, y3);
+          // a-side factors: (s alpha Y_a[c]) and (s lam Y_a[c]) duplicated, and the
+          // column pairs (Y_a[0], Y_a[1]) of the d = 2 entries
+          const T p0 = sal * y0, p1 = sal * y1, p2 = sal * y2;
+          const T l0 = slam * y0, l1 = slam * y1, l2 = slam * y2;
+          const V2 P0 = vmk(p0, p0), P1 = vmk(p1, p1), P2 = vmk(p2, p2), PC = vmk(p0, p1);
+          const V2 L0 = vmk(l0, l0), L1 = vmk(l1, l1), L2 = vmk(l2, l2), LC = vmk(l0, l1);
+          V2 Z01 = vmk(T(0), T(0));
+          T Z2 = T(0);
+          if constexpr (NEO) {
+            T z0, z1, z2, z3;
+            ld4(yr + RL + 4 * a, z0, z1, z2, z3);
+            Z01 = vmk(z0, z1);
+            Z2 = z2;
+          }
 #pragma unroll
-        for (int i = 0; i < BB; ++i) {
-          if (i < nb) {
-            T gb[8];
-            ld<8>(Gb + GY * (b0 + i), gb);
-            const T dot = smu * (ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2]);
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-              for (int d = 0; d < 3; ++d)
-                acc[i][3 * c + d] = fma(ay[d], gb[4 + c], fma(ly[c], gb[4 + d], acc[i][3 * c + d] + (c == d ? dot : T(0))));
+          for (int i = 0; i < BB; ++i) {
+            if (i < nb) {
+              T b0v, b1v, b2v, b3v;
+              ld4(yr + 4 * (b0 + i), b0v, b1v, b2v, b3v);
+              const V2 Y01 = vmk(b0v, b1v), Y22 = vmk(b2v, b3v);
+              w1r[i][0] = vfma(P0, Y01, w1r[i][0]);
+              w1r[i][1] = vfma(P1, Y01, w1r[i][1]);
+              w1r[i][2] = vfma(P2, Y01, w1r[i][2]);
+              w1c[i] = vfma(PC, Y22, w1c[i]);
+              w1s[i] = fma(p2, b2v, w1s[i]);
+              w2r[i][0] = vfma(L0, Y01, w2r[i][0]);
+              w2r[i][1] = vfma(L1, Y01, w2r[i][1]);
+              w2r[i][2] = vfma(L2, Y01, w2r[i][2]);
+              w2c[i] = vfma(LC, Y22, w2c[i]);
+              w2s[i] = fma(l2, b2v, w2s[i]);
+              if constexpr (NEO) {
+                dd[i] = vfma(Z01, Y01, dd[i]);
+                ds[i] = fma(Z2, b2v, ds[i]);
+              }
+            }
           }
         }
       }
-      if (qq + 1 < Q) rows(qq + 1);  // the other buffer, last read at point qq - 1
+      if (g + 1 < ngroups) make_rows(g + 1);  // the other buffer, last read in group g - 1
       __syncthreads();
     }
     if (owner) {
-      T* o = stage + (size_t)te * NN + (3 * a) * N + 3 * b0;
+      T* st = stage + (size_t)te * NN;
 #pragma unroll
-      for (int i = 0; i < BB; ++i)
-        if (i < nb)
+      for (int i = 0; i < BB; ++i) {
+        if (i < nb) {
+          // W[c][d]: rows c = 0..2 hold d = 0, 1; the column pair holds (0, 2), (1, 2); the scalar (2, 2)
+          const T W1[9] = {w1r[i][0].x, w1r[i][0].y, w1c[i].x, w1r[i][1].x, w1r[i][1].y, w1c[i].y,
+                           w1r[i][2].x, w1r[i][2].y, w1s[i]};
+          const T W2[9] = {w2r[i][0].x, w2r[i][0].y, w2c[i].x, w2r[i][1].x, w2r[i][1].y, w2c[i].y,
+                           w2r[i][2].x, w2r[i][2].y, w2s[i]};
+          const T D = NEO ? (dd[i].x + dd[i].y) + ds[i] : (W1[0] + W1[4]) + W1[8];
+          T v[9];
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) o[c * N + 3 * i + d] = acc[i][3 * c + d];
+            for (int d = 0; d < 3; ++d) v[3 * c + d] = (c == d ? D : T(0)) + W1[3 * d + c] + W2[3 * c + d];
+          put_sym_block<N, T>(st, a, b0 + i, v);
+        }
+      }
     }
     __syncthreads();
     store_tile<NT, T>(q.out, e0 * NN, stage, ne * NN, q.out_f32);
