@@ -187,9 +187,9 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
   if (variant == FEA_VARIANT_NAIVE && prec != 0) return fail(FEA_EINVAL, "the plain variant is FP64 only");
   if (variant == FEA_VARIANT_PRE && pre_terms(form, p) == 0)
     return fail(FEA_EINVAL, "pre-evaluation does not apply to this form (integrand not polynomial)");
-  const KernelInfo* k = batch ? find_batch_kernel(variant, form, p) : find_kernel(variant, form, p, prec);
-  if (!k) return fail(FEA_EINVAL, "no kernel for this variant/form/degree/precision");
   const int Q = rule_points(rule_index(form, p));
+  const KernelInfo* k = batch ? find_batch_kernel(variant, form, p) : find_kernel(variant, form, p, prec, budget, Q);
+  if (!k) return fail(FEA_EINVAL, "no kernel for this variant/form/degree/precision");
   int TE = o.tile;
   if (TE < 0) return fail(FEA_EINVAL, "negative tile");
   // tuned tiles were measured on the standalone kernels; the batch keeps its own rule

@@ -25,7 +25,10 @@ extern const int kNumNaiveKernels;
 extern const KernelInfo kPreTileF32[];
 extern const int kNumPreTileF32;
 
-const KernelInfo* find_kernel(int variant, int form, int p, int prec);
+// The first registered kernel of (variant, form, degree, precision) whose
+// one-element tile fits `budget` bytes of shared memory (any, if none does or
+// budget is 0).
+const KernelInfo* find_kernel(int variant, int form, int p, int prec, size_t budget = 0, int Q = 0);
 // Tile functions of the batched persistent kernel (FP32): PreTile / SeTile.
 const KernelInfo* find_batch_kernel(int variant, int form, int p);
 

@@ -14,15 +14,19 @@ const KernelInfo kNaiveKernels[] = {
 #undef NV
 const int kNumNaiveKernels = sizeof(kNaiveKernels) / sizeof(kNaiveKernels[0]);
 
-const KernelInfo* find_kernel(int variant, int form, int p, int prec) {
+const KernelInfo* find_kernel(int variant, int form, int p, int prec, size_t budget, int Q) {
   const KernelInfo* tabs[3] = {kNaiveKernels, kSeKernels, kPreKernels};
   const int counts[3] = {kNumNaiveKernels, kNumSeKernels, kNumPreKernels};
   if (variant < 0 || variant > 2) return nullptr;
+  const KernelInfo* any = nullptr;
   for (int i = 0; i < counts[variant]; ++i) {
     const KernelInfo& k = tabs[variant][i];
-    if (k.form == form && k.p == p && k.prec == prec) return &k;
+    if (k.form != form || k.p != p || k.prec != prec) continue;
+    // the first registered kernel whose smallest tile fits the budget (Constraint 2)
+    if (budget == 0 || k.smem(1, Q) <= budget) return &k;
+    if (!any) any = &k;
   }
-  return nullptr;
+  return any;
 }
 
 }  // namespace fea
@@ -34,7 +38,7 @@ const KernelInfo* find_batch_kernel(int variant, int form, int p) {
       if (kPreTileF32[i].form == form && kPreTileF32[i].p == p) return &kPreTileF32[i];
     return nullptr;
   }
-  if (variant == V_SE) return find_kernel(V_SE, form, p, 1);
+  if (variant == V_SE) return find_kernel(V_SE, form, p, 1, 0, 0);
   return nullptr;
 }
 }  // namespace fea

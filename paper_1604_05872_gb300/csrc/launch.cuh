@@ -14,8 +14,15 @@ __device__ __forceinline__ unsigned dynamic_smem_bytes() {
 }
 constexpr unsigned ERR_LAUNCH = 4u;
 
+// Tile functions that need a given number of resident CTAs per SM (register
+// budget) say so with a MINB constant.
+template <class K, class = void>
+struct MinBlocksOf { static constexpr int value = 1; };
 template <class K>
-__global__ void __launch_bounds__(NT) run_tiles(Req q, unsigned* err) {
+struct MinBlocksOf<K, std::void_t<decltype(K::MINB)>> { static constexpr int value = K::MINB; };
+
+template <class K>
+__global__ void __launch_bounds__(NT, MinBlocksOf<K>::value) run_tiles(Req q, unsigned* err) {
   extern __shared__ __align__(16) char smem_raw[];
   // a tile larger than the shared memory it was launched with is refused, not run
   if (K::smem(q.tile, q.Q) > dynamic_smem_bytes()) {

@@ -25,6 +25,65 @@
 
 namespace fea {
 
+// Per-element record of the pre-evaluated elasticity kernels, from the FP64
+// geometry: adj[9], M = adj adj^T [9], mu[4], lam[4], 1/|det J| (NaN for a
+// degenerate element), pad to 32.
+template <typename T>
+__device__ __forceinline__ void pre_vec_record(const double* x, const double* c, T* g, unsigned* err) {
+  double adj[9];
+  const double det = geometry_fp64(x, adj);
+  const bool bad = !(fabs(det) > 0.0) || !isfinite(det);
+  if (bad) flag_error(err, ERR_DEGENERATE);
+  T a[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) g[k] = a[k] = from_double<T>(adj[k]);
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int be = 0; be < 3; ++be)
+      g[9 + 3 * al + be] = a[3 * al] * a[3 * be] + a[3 * al + 1] * a[3 * be + 1] + a[3 * al + 2] * a[3 * be + 2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) g[18 + k] = from_double<T>(c[k]);
+  const T nan = T(__int_as_float(0x7fc00000));
+  g[26] = bad ? nan : T(1) / from_double<T>(fabs(det));
+}
+
+// One 3x3 block (a, b) from the pair's 36 reference values R_(k,al,be) and the
+// element record g: v = (tr(M X) I + adj^T (X^T + L) adj) / |det J|.
+template <typename T>
+__device__ __forceinline__ void pre_vec_block(const T* g, const T (&R)[36], T (&v)[9]) {
+  T X[9], Lm[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    X[k] = g[18] * R[k] + g[19] * R[9 + k] + g[20] * R[18 + k] + g[21] * R[27 + k];
+    Lm[k] = g[22] * R[k] + g[23] * R[9 + k] + g[24] * R[18 + k] + g[25] * R[27 + k];
+  }
+  T tr = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) tr = fma(g[9 + k], X[k], tr);
+  // Z = X^T + L;  P = Z adj;  A = adj^T P
+  T Pm[9];
+#pragma unroll
+  for (int al = 0; al < 3; ++al)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T x = T(0);
+#pragma unroll
+      for (int be = 0; be < 3; ++be) x = fma(X[3 * be + al] + Lm[3 * al + be], g[3 * be + d], x);
+      Pm[3 * al + d] = x;
+    }
+  const T inv = g[26];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T x = c == d ? tr : T(0);
+#pragma unroll
+      for (int al = 0; al < 3; ++al) x = fma(g[3 * al + c], Pm[3 * al + d], x);
+      v[3 * c + d] = x * inv;
+    }
+}
+
 template <int P, typename T>
 struct PreVecTile {
   static constexpr int FORM = 2;
@@ -55,25 +114,7 @@ struct PreVecTile {
     load_doubles<NT>(xs, q.coords + e0 * 12, ne * 12);
     load_doubles<NT>(cs, q.coeffs + e0 * CLEN, ne * CLEN);
     __syncthreads();
-    if (tid < ne) {  // FP64 geometry; FP32 (or FP64) per-element record
-      double adj[9];
-      const double det = geometry_fp64(xs + 12 * tid, adj);
-      const bool bad = !(fabs(det) > 0.0) || !isfinite(det);
-      if (bad) flag_error(err, ERR_DEGENERATE);
-      T* g = geo + GEO * tid;
-      T a[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) g[k] = a[k] = from_double<T>(adj[k]);
-#pragma unroll
-      for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be)
-          g[9 + 3 * al + be] = a[3 * al] * a[3 * be] + a[3 * al + 1] * a[3 * be + 1] + a[3 * al + 2] * a[3 * be + 2];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) g[18 + k] = from_double<T>(cs[CLEN * tid + k]);
-      const T nan = T(__int_as_float(0x7fc00000));
-      g[26] = bad ? nan : T(1) / from_double<T>(fabs(det));
-    }
+    if (tid < ne) pre_vec_record<T>(xs + 12 * tid, cs + CLEN * tid, geo + GEO * tid, err);
     __syncthreads();
 
     for (int k = tid; k < NP; k += NT) {
@@ -84,38 +125,8 @@ struct PreVecTile {
 #pragma unroll
       for (int r = 0; r < 36; ++r) R[r] = __ldg(Rg + (size_t)r * S + s);
       for (int e = 0; e < ne; ++e) {
-        const T* g = geo + GEO * e;
-        T X[9], Lm[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          X[k] = g[18] * R[k] + g[19] * R[9 + k] + g[20] * R[18 + k] + g[21] * R[27 + k];
-          Lm[k] = g[22] * R[k] + g[23] * R[9 + k] + g[24] * R[18 + k] + g[25] * R[27 + k];
-        }
-        T tr = T(0);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) tr = fma(g[9 + k], X[k], tr);
-        // Z = X^T + L;  P = Z adj;  A = adj^T P
-        T Pm[9];
-#pragma unroll
-        for (int al = 0; al < 3; ++al)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            T v = T(0);
-#pragma unroll
-            for (int be = 0; be < 3; ++be) v = fma(X[3 * be + al] + Lm[3 * al + be], g[3 * be + d], v);
-            Pm[3 * al + d] = v;
-          }
-        const T inv = g[26];
         T v[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            T x = c == d ? tr : T(0);
-#pragma unroll
-            for (int al = 0; al < 3; ++al) x = fma(g[3 * al + c], Pm[3 * al + d], x);
-            v[3 * c + d] = x * inv;
-          }
+        pre_vec_block<T>(geo + GEO * e, R, v);
         put_sym_block<N, T>(stage + (size_t)e * NN, a, b, v);
       }
     }

@@ -24,10 +24,14 @@
 // Thread layout: EF consecutive lanes take EF elements of the tile with the same
 // run, so a warp holds 32 / EF runs of (nearly) equal length and reads the rows
 // of EF elements at once (element rows are an odd number of 16-byte slots
-// apart: conflict-free).  Pointwise data (Neo-Hookean: F, F^-1, ln det F, in
-// the tile's precision) are computed for every (element, point) up front; the
+// apart: conflict-free).  Pointwise data are computed for every (element,
+// point) up front; for Neo-Hookean, F = I + grad u is widened to FP64 and
+// det F, F^-1 and ln det F are evaluated in FP64 (FP32 path included).  The
 // (Y, Z) rows of the next QG points are formed while the current QG points
-// accumulate (double buffer, one barrier per QG points).
+// accumulate (double buffer, one barrier per QG points; the point count is
+// padded to a multiple of QG with zero-weight points so that the point loop
+// unrolls).  The staged element matrices reuse the pointwise and row buffers,
+// which are dead once the last point group has been accumulated.
 #pragma once
 #include "common.cuh"
 #include "sym.cuh"
@@ -43,16 +47,17 @@ struct SeVecTile {
   static constexpr int N = 3 * NS;
   static constexpr int NN = N * N;
   static constexpr int CLEN = coeff_len_c(FORM, P);
-  // trial functions per thread and elements interleaved per warp
-  static constexpr int BB = F32 ? (P == 1 ? 2 : P == 4 ? 3 : 4) : (P == 4 ? 3 : 2);
-  static constexpr int EF = P == 1 ? 8 : P == 2 ? (F32 ? 4 : 8) : P == 3 ? (F32 ? 4 : 2) : 1;
+  // trial functions per thread, elements interleaved per warp, resident CTAs per SM
+  static constexpr int BB = F32 ? (P <= 2 ? 2 : P == 3 ? 4 : 3) : (P == 4 ? 3 : 2);
+  static constexpr int EF = P <= 2 ? 8 : P == 3 ? (F32 ? 4 : 2) : 1;
+  static constexpr int MINB = F32 ? (P <= 2 ? 3 : 2) : 1;
   using Chunks = SymChunks<NS, BB>;
   static constexpr int NCH = Chunks::NCH;
   static constexpr int GROUPS = NT / (EF * NCH);
   static_assert(GROUPS >= 1, "one element group must fit the CTA");
   static constexpr int TEMAX = EF * GROUPS;
   static constexpr int NSP = NS | 1;                 // row slots per element (odd)
-  static constexpr int QG = 3;                       // points per barrier
+  static constexpr int QG = 4;                       // points per barrier
   static constexpr int GEO = 12;                     // Jinv[9], |det|, pad
   static constexpr int PW = NEO ? 20 : 4;            // per (e, q): [Fi[9], s mu F[9],] s alpha, s lam
   static constexpr int RW = NEO ? 2 : 1;             // 16-byte rows per (e, a): Y [, Z]
@@ -60,14 +65,19 @@ struct SeVecTile {
 
   FEA_HD static int max_tile() { return TEMAX; }
   FEA_HD static int pref_tile() { return TEMAX; }
+  FEA_HD static int qpad(int Q) { return (Q + QG - 1) / QG * QG; }
   FEA_HD static size_t off_c(int TE) { return round_up_sz((size_t)TE * 12 * 8, 16); }
   FEA_HD static size_t off_ct(int TE) { return off_c(TE) + round_up_sz((size_t)TE * CLEN * 8, 16); }
   FEA_HD static size_t off_geo(int TE) { return off_ct(TE) + round_up_sz((size_t)TE * CLEN * sizeof(T), 16); }
   FEA_HD static size_t off_pw(int TE) { return off_geo(TE) + round_up_sz((size_t)TE * GEO * sizeof(T), 16); }
-  FEA_HD static size_t off_rows(int TE, int Q) { return off_pw(TE) + round_up_sz((size_t)TE * Q * PW * sizeof(T), 16); }
+  FEA_HD static size_t off_rows(int TE, int Q) { return off_pw(TE) + round_up_sz((size_t)TE * qpad(Q) * PW * sizeof(T), 16); }
   FEA_HD static size_t rows_len(int TE) { return (size_t)QG * TE * NSP * 4; }  // T per buffer and row kind
-  FEA_HD static size_t off_stage(int TE, int Q) { return off_rows(TE, Q) + (size_t)2 * RW * rows_len(TE) * sizeof(T); }
-  FEA_HD static size_t smem(int TE, int Q) { return off_stage(TE, Q) + round_up_sz((size_t)TE * NN * sizeof(T), 16); }
+  FEA_HD static size_t off_stage(int TE) { return off_pw(TE); }                  // aliases pointwise data and rows
+  FEA_HD static size_t smem(int TE, int Q) {
+    const size_t a = off_stage(TE) + round_up_sz((size_t)TE * NN * sizeof(T), 16);
+    const size_t b = off_rows(TE, Q) + (size_t)2 * RW * rows_len(TE) * sizeof(T);
+    return a > b ? a : b;
+  }
 
   __device__ static void tile(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
     const int TE = q.tile, Q = q.Q;
@@ -77,7 +87,7 @@ struct SeVecTile {
     T* geo = reinterpret_cast<T*>(sm + off_geo(TE));
     T* PWs = reinterpret_cast<T*>(sm + off_pw(TE));
     T* rows = reinterpret_cast<T*>(sm + off_rows(TE, Q));   // [2][RW][QG][TE][NSP][4]
-    T* stage = reinterpret_cast<T*>(sm + off_stage(TE, Q));
+    T* stage = reinterpret_cast<T*>(sm + off_stage(TE));
     const size_t RL = rows_len(TE);
     const TabLayout L = tab_layout(Q, NS, 0);
     const T* tab = reinterpret_cast<const T*>(q.tab);
@@ -113,11 +123,17 @@ struct SeVecTile {
     const T mu_c = NEO ? from_double<T>(q.coeffs[q.E * CLEN]) : T(0);
     const T lam_c = NEO ? from_double<T>(q.coeffs[q.E * CLEN + 1]) : T(0);
 
-    // pointwise data of every (element, point) of the tile
-    for (int w = tid; w < ne * Q; w += NT) {
-      const int e = w / Q, qq = w - e * Q;
-      const T* Ji = geo + GEO * e;
+    // pointwise data of every (element, point) of the tile; padded points get zero weight
+    const int QP = qpad(Q);
+    for (int w = tid; w < ne * QP; w += NT) {
+      const int e = w / QP, qq = w - e * QP;
       T* o = PWs + PW * w;
+      if (qq >= Q) {
+#pragma unroll
+        for (int k = 0; k < PW; ++k) o[k] = T(0);
+        continue;
+      }
+      const T* Ji = geo + GEO * e;
       const T s = Wt[qq] * Ji[9];
       if constexpr (!NEO) {
         T mu = T(0), lam = T(0);
@@ -129,7 +145,7 @@ struct SeVecTile {
         o[PW - 2] = s * mu;   // alpha = mu
         o[PW - 1] = s * lam;
       } else {
-        // grad u = (sum_a u_a (x) grad_X Phi_a) J^-1
+        // grad u = (sum_a u_a (x) grad_X Phi_a) J^-1 in the tile precision
         const T* u = ct + CLEN * e;
         T gr[9];
 #pragma unroll
@@ -145,34 +161,39 @@ struct SeVecTile {
             gr[3 * i + 2] = fma(ui, d2, gr[3 * i + 2]);
           }
         }
-        T F[9];
+        T gu[9];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int x = 0; x < 3; ++x)
-            F[3 * i + x] = (i == x ? T(1) : T(0)) + gr[3 * i] * Ji[x] + gr[3 * i + 1] * Ji[3 + x] + gr[3 * i + 2] * Ji[6 + x];
-        T cof[9];  // det(F) F^-1
-        cof[0] = F[4] * F[8] - F[5] * F[7];
-        cof[1] = F[2] * F[7] - F[1] * F[8];
-        cof[2] = F[1] * F[5] - F[2] * F[4];
-        cof[3] = F[5] * F[6] - F[3] * F[8];
-        cof[4] = F[0] * F[8] - F[2] * F[6];
-        cof[5] = F[2] * F[3] - F[0] * F[5];
-        cof[6] = F[3] * F[7] - F[4] * F[6];
-        cof[7] = F[1] * F[6] - F[0] * F[7];
-        cof[8] = F[0] * F[4] - F[1] * F[3];
-        const T dF = F[0] * cof[0] + F[1] * cof[3] + F[2] * cof[6];
-        const bool bad = !(dF > T(0)) || !isfinite(dF);
+          for (int x = 0; x < 3; ++x) gu[3 * i + x] = gr[3 * i] * Ji[x] + gr[3 * i + 1] * Ji[3 + x] + gr[3 * i + 2] * Ji[6 + x];
+        // F = I + grad u, det F, F^-1 and ln det F in FP64
+        double F[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          if constexpr (F32) F[k] = f2d(gu[k]);
+          else F[k] = gu[k];
+        }
+        F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
+        double cof[9];  // det(F) F^-1
+        cof[0] = fma(F[4], F[8], -F[5] * F[7]);
+        cof[1] = fma(F[2], F[7], -F[1] * F[8]);
+        cof[2] = fma(F[1], F[5], -F[2] * F[4]);
+        cof[3] = fma(F[5], F[6], -F[3] * F[8]);
+        cof[4] = fma(F[0], F[8], -F[2] * F[6]);
+        cof[5] = fma(F[2], F[3], -F[0] * F[5]);
+        cof[6] = fma(F[3], F[7], -F[4] * F[6]);
+        cof[7] = fma(F[1], F[6], -F[0] * F[7]);
+        cof[8] = fma(F[0], F[4], -F[1] * F[3]);
+        const double dF = fma(F[0], cof[0], fma(F[1], cof[3], F[2] * cof[6]));
+        const bool bad = !(dF > 0.0) || !isfinite(dF);
         if (bad) flag_error(err, ERR_DEGENERATE);
-        const T idF = T(1) / dF;
-        T lnJ;
-        if constexpr (F32) lnJ = logf(dF);
-        else lnJ = log(dF);
+        const double idF = 1.0 / dF;
+        const T lnJ = from_double<T>(log(dF));
         const T smu = s * mu_c;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          o[k] = bad ? nan : cof[k] * idF;  // o[3 i + j] = Fi[i][j]
-          o[9 + k] = bad ? nan : smu * F[k];
+          o[k] = bad ? nan : from_double<T>(cof[k] * idF);  // o[3 i + j] = Fi[i][j]
+          o[9 + k] = bad ? nan : smu * ((k % 4 == 0 ? T(1) : T(0)) + gu[k]);
         }
         o[PW - 2] = bad ? nan : s * (mu_c - lam_c * lnJ);
         o[PW - 1] = s * lam_c;
@@ -181,25 +202,26 @@ struct SeVecTile {
     __syncthreads();
 
     // rows of points [g QG, g QG + QG) into buffer g & 1: Y = (Y0, Y1, Y2, Y2), Z = (Z0, Z1, Z2, 0)
-    const int ngroups = (Q + QG - 1) / QG;
+    const int ngroups = QP / QG;
+    const int rows_items = ne * NS;
     auto make_rows = [&](int g) {
       T* Yb = rows + (size_t)(g & 1) * RW * RL;
       const int q0 = g * QG;
-      const int nq = Q - q0 < QG ? Q - q0 : QG;
-      for (int w = tid; w < nq * ne * NS; w += NT) {
-        const int qi = w / (ne * NS), r = w - qi * (ne * NS);
+      for (int w = tid; w < QG * rows_items; w += NT) {
+        const int qi = w / rows_items, r = w - qi * rows_items;
         const int e = r / NS, a = r - e * NS;
         const int qq = q0 + qi;
         const T* Ji = geo + GEO * e;
-        const T* dp = dphi + (qq * NS + a) * 3;
-        const T d0 = dp[0], d1 = dp[1], d2 = dp[2];
+        const T live = qq < Q ? T(1) : T(0);   // padded points: zero rows
+        const T* dp = dphi + ((qq < Q ? qq : 0) * NS + a) * 3;
+        const T d0 = live * dp[0], d1 = live * dp[1], d2 = live * dp[2];
         T G[3];
 #pragma unroll
         for (int x = 0; x < 3; ++x) G[x] = Ji[x] * d0 + Ji[3 + x] * d1 + Ji[6 + x] * d2;
         const size_t slot = (((size_t)qi * TE + e) * NSP + a) * 4;
         T Y[3];
         if constexpr (NEO) {
-          const T* pw = PWs + PW * (e * Q + qq);
+          const T* pw = PWs + PW * (e * QP + qq);
 #pragma unroll
           for (int x = 0; x < 3; ++x) Y[x] = G[0] * pw[x] + G[1] * pw[3 + x] + G[2] * pw[6 + x];
           T* z = Yb + RL + slot;
@@ -238,10 +260,10 @@ struct SeVecTile {
       if (owner) {
         const T* Yb = rows + (size_t)(g & 1) * RW * RL;
         const int q0 = g * QG;
-        const int nq = Q - q0 < QG ? Q - q0 : QG;
-        for (int qi = 0; qi < nq; ++qi) {
+#pragma unroll
+        for (int qi = 0; qi < QG; ++qi) {
           const T* yr = Yb + (((size_t)qi * TE + te) * NSP) * 4;
-          const T* pw = PWs + PW * (te * Q + q0 + qi);
+          const T* pw = PWs + PW * (te * QP + q0 + qi);
           const T sal = pw[PW - 2], slam = pw[PW - 1];
           T y0, y1, y2, y3;
           ld4(yr + 4 * a, y0, y1, y2, y3);
