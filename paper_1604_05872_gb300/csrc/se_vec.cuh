@@ -38,6 +38,22 @@
 
 namespace fea {
 
+// Four T to 16-byte aligned shared memory.
+template <typename T>
+__device__ __forceinline__ void st4(T* p, T x, T y, T z, T w) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x, y, z, w);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(x, y);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(z, w);
+  }
+}
+
+// floor(w / d) without an integer division: truncate (w + 1/2) * fl(1/d) in
+// FP32 (correctly rounded reciprocal and product).  Exact for 0 <= w < 16384
+// and 1 <= d < 8192, checked exhaustively; the tile loops stay far inside.
+__device__ __forceinline__ int small_div(int w, float inv_d) { return (int)(((float)w + 0.5f) * inv_d); }
+
 template <int FORM, int P, typename T>
 struct SeVecTile {
   static_assert(FORM == 2 || FORM == 3, "vector forms");
@@ -125,8 +141,9 @@ struct SeVecTile {
 
     // pointwise data of every (element, point) of the tile; padded points get zero weight
     const int QP = qpad(Q);
+    const float inv_qp = 1.0f / (float)QP;
     for (int w = tid; w < ne * QP; w += NT) {
-      const int e = w / QP, qq = w - e * QP;
+      const int e = small_div(w, inv_qp), qq = w - e * QP;
       T* o = PWs + PW * w;
       if (qq >= Q) {
 #pragma unroll
@@ -187,12 +204,14 @@ struct SeVecTile {
         const double dF = fma(F[0], cof[0], fma(F[1], cof[3], F[2] * cof[6]));
         const bool bad = !(dF > 0.0) || !isfinite(dF);
         if (bad) flag_error(err, ERR_DEGENERATE);
-        const double idF = 1.0 / dF;
+        // the cancellation-prone cofactors and det F are FP64; the division by
+        // det F is a well-conditioned scaling done after rounding to T
+        const T idF = T(1) / from_double<T>(dF);
         const T lnJ = from_double<T>(log(dF));
         const T smu = s * mu_c;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          o[k] = bad ? nan : from_double<T>(cof[k] * idF);  // o[3 i + j] = Fi[i][j]
+          o[k] = bad ? nan : from_double<T>(cof[k]) * idF;  // o[3 i + j] = Fi[i][j]
           o[9 + k] = bad ? nan : smu * ((k % 4 == 0 ? T(1) : T(0)) + gu[k]);
         }
         o[PW - 2] = bad ? nan : s * (mu_c - lam_c * lnJ);
@@ -204,35 +223,42 @@ struct SeVecTile {
     // rows of points [g QG, g QG + QG) into buffer g & 1: Y = (Y0, Y1, Y2, Y2), Z = (Z0, Z1, Z2, 0)
     const int ngroups = QP / QG;
     const int rows_items = ne * NS;
+    const float inv_items = 1.0f / (float)rows_items;
     auto make_rows = [&](int g) {
       T* Yb = rows + (size_t)(g & 1) * RW * RL;
       const int q0 = g * QG;
       for (int w = tid; w < QG * rows_items; w += NT) {
-        const int qi = w / rows_items, r = w - qi * rows_items;
+        const int qi = small_div(w, inv_items), r = w - qi * rows_items;
         const int e = r / NS, a = r - e * NS;
         const int qq = q0 + qi;
         const T* Ji = geo + GEO * e;
+        T j[12];
+        ld4(Ji, j[0], j[1], j[2], j[3]);
+        ld4(Ji + 4, j[4], j[5], j[6], j[7]);
+        ld4(Ji + 8, j[8], j[9], j[10], j[11]);
         const T live = qq < Q ? T(1) : T(0);   // padded points: zero rows
         const T* dp = dphi + ((qq < Q ? qq : 0) * NS + a) * 3;
         const T d0 = live * dp[0], d1 = live * dp[1], d2 = live * dp[2];
         T G[3];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) G[x] = Ji[x] * d0 + Ji[3 + x] * d1 + Ji[6 + x] * d2;
+        for (int x = 0; x < 3; ++x) G[x] = j[x] * d0 + j[3 + x] * d1 + j[6 + x] * d2;
         const size_t slot = (((size_t)qi * TE + e) * NSP + a) * 4;
         T Y[3];
         if constexpr (NEO) {
           const T* pw = PWs + PW * (e * QP + qq);
+          T f[20];
 #pragma unroll
-          for (int x = 0; x < 3; ++x) Y[x] = G[0] * pw[x] + G[1] * pw[3 + x] + G[2] * pw[6 + x];
-          T* z = Yb + RL + slot;
+          for (int k = 0; k < 20; k += 4) ld4(pw + k, f[k], f[k + 1], f[k + 2], f[k + 3]);
 #pragma unroll
-          for (int i = 0; i < 3; ++i) z[i] = pw[9 + 3 * i] * G[0] + pw[10 + 3 * i] * G[1] + pw[11 + 3 * i] * G[2];
-          z[3] = T(0);
+          for (int x = 0; x < 3; ++x) Y[x] = G[0] * f[x] + G[1] * f[3 + x] + G[2] * f[6 + x];
+          T z[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) z[i] = f[9 + 3 * i] * G[0] + f[10 + 3 * i] * G[1] + f[11 + 3 * i] * G[2];
+          st4(Yb + RL + slot, z[0], z[1], z[2], T(0));
         } else {
           Y[0] = G[0]; Y[1] = G[1]; Y[2] = G[2];
         }
-        T* y = Yb + slot;
-        y[0] = Y[0]; y[1] = Y[1]; y[2] = Y[2]; y[3] = Y[2];
+        st4(Yb + slot, Y[0], Y[1], Y[2], Y[2]);
       }
     };
 
@@ -264,7 +290,8 @@ struct SeVecTile {
         for (int qi = 0; qi < QG; ++qi) {
           const T* yr = Yb + (((size_t)qi * TE + te) * NSP) * 4;
           const T* pw = PWs + PW * (te * QP + q0 + qi);
-          const T sal = pw[PW - 2], slam = pw[PW - 1];
+          const V2 sw = *reinterpret_cast<const V2*>(pw + PW - 2);
+          const T sal = sw.x, slam = sw.y;
           T y0, y1, y2, y3;
           ld4(yr + 4 * a, y0, y1, y2, y3);
           // a-side factors: (s alpha Y_a[c]) and (s lam Y_a[c]) duplicated, and the
