@@ -39,7 +39,7 @@ __device__ __forceinline__ void run_one(const Req& q, int64_t t, char* sm, unsig
   K::tile(q, e0, (int)(left < q.tile ? left : q.tile), sm, err);
 }
 
-__global__ void __launch_bounds__(NT) batch_kernel(const Req* __restrict__ reqs, int nreq, long long total,
+__global__ void __launch_bounds__(NT, 2) batch_kernel(const Req* __restrict__ reqs, int nreq, long long total,
                                                    unsigned long long* counter, unsigned* err) {
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ long long s_w;
