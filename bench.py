@@ -219,14 +219,15 @@ WORKLOADS = {
     "neohookean_p2_500k": (3, 2, 500_000, False),
 }
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flops x max clock
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12     # SMs x FP64 lanes per clock x 2 flops x max clock
+FP64_PEAK_TINSTR = 152 * 2 * 2.07e9 / 1e12          # SMs x FP64 lanes per clock x max clock (lane-instructions)
 
 
 def fp64_ops_per_element(form, p, variant, Q):
-    """FP64 operations per element of the flop-reduced kernels: 30 for the
-    geometry (J, adjugate, det), plus about 70 per point for the Neo-Hookean
-    det F, F^-1 and ln det F."""
-    return 30 + (70 * Q if form == 3 else 0)
+    """FP64 lane-instructions per element of the flop-reduced kernels: 30 for
+    the geometry (9 subtractions for J, 18 for the adjugate's 2x2 minors, 3 for
+    det J), plus, per Neo-Hookean point, 21 for the cofactors of F and det F
+    and about 20 for ln det F."""
+    return 30 + (41 * Q if form == 3 else 0)
 
 
 def main():
@@ -239,6 +240,7 @@ def main():
     ap.add_argument("--elements", type=int, default=0, help="override the element count")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--tuning", default="", help="tuning JSON (records + MLP) for the stream workload")
+    ap.add_argument("--out-f32", action="store_true", help="FP32 output (element matrices stored as float)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -285,20 +287,23 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     coords, coeffs = inputs.workload(form, p, E, seed=inputs.SEED + rank, anisotropic=aniso)  # own shard per rank
     c = torch.from_numpy(coords).cuda()
     fc = None if form == 0 else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
-    out = fea.empty_out(form, p, E)
+    f32 = bool(args.out_f32)
+    out = fea.empty_out(form, p, E, out_f32=f32)
     n = out.shape[1]
+    esz = 4 if f32 else 8
     stream = torch.cuda.current_stream()
     pl = fea.plan(form, p)
+    bytes_elem = 96 + 8 * fea.coeff_len(form, p) + esz * n * n
 
     for _ in range(args.warmup):
-        fea.assemble(form, p, c, fc, out=out)
+        fea.assemble(form, p, c, fc, out=out, out_f32=f32)
     fea.sync()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            fea.assemble(form, p, c, fc, out=out)
+            fea.assemble(form, p, c, fc, out=out, out_f32=f32)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -308,12 +313,13 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
 
     # plain FP64 comparator on the same workload (a bounded prefix of it for the slowest forms)
     En = int(min(E, max(1000, 0.5e12 / pl["flops_naive"])))
-    fea.assemble(form, p, c[:En], fc, out=out[:En], precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
+    out64 = out if not f32 else fea.empty_out(form, p, En)
+    fea.assemble(form, p, c[:En], fc, out=out64[:En], precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
     barrier()
     nsteps = 2
     ev0.record(stream)
     for _ in range(nsteps):
-        fea.assemble(form, p, c[:En], fc, out=out[:En], precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
+        fea.assemble(form, p, c[:En], fc, out=out64[:En], precision=fea.PREC_FP64, variant=fea.VARIANT_NAIVE)
     ev1.record(stream)
     barrier()
     ms_naive = ev0.elapsed_time(ev1) / nsteps
@@ -323,24 +329,25 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     # end to end through the host-buffer C ABI call (copies inside the timed region)
     hc = torch.from_numpy(coords).pin_memory()
     hf = None if fc is None else fc.cpu().pin_memory()
-    ho = torch.empty((E, n, n), dtype=torch.float64).pin_memory()
+    del out64
+    ho = torch.empty((E, n, n), dtype=torch.float32 if f32 else torch.float64).pin_memory()
     for _ in range(2):
-        fea.assemble_host(form, p, hc, hf, ho)
+        fea.assemble_host(form, p, hc, hf, ho, out_f32=f32)
     barrier()
     e2e_steps = max(3, args.steps // 4)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fea.assemble_host(form, p, hc, hf, ho)
+        fea.assemble_host(form, p, hc, hf, ho, out_f32=f32)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3)
 
     hbm, peak_kind = peaks()
-    alg_bytes = E * pl["bytes"]
+    alg_bytes = E * bytes_elem
     flops = E * pl["flops_run"]
     f64 = E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"])
     t_hbm = alg_bytes / (hbm * 1e9)
     t_f32 = flops / (FP32_PEAK_TFLOPS * 1e12)
-    t_f64 = f64 / (FP64_PEAK_TFLOPS * 1e12)
+    t_f64 = f64 / (FP64_PEAK_TINSTR * 1e12)
     if t_hbm >= max(t_f32, t_f64):
         roof = {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_kind": peak_kind}
@@ -348,14 +355,14 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_kind": "derived: FP32 lanes x clock"}
     else:
-        roof = {"bound": "alu", "achieved": f64 / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64)", "peak_kind": "derived: FP64 lanes x clock"}
+        roof = {"bound": "alu", "achieved": f64 / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TINSTR,
+                "unit": "T FP64 lane-instructions/s", "peak_kind": "derived: FP64 lanes x clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = profiled_traffic() if args.workload == "helmholtz_p2_1M" and E == E0 else None
+    roof["traffic"] = profiled_traffic() if args.workload == "helmholtz_p2_1M" and E == E0 and not f32 else None
     roof["alg_bytes_per_launch"] = alg_bytes
     roof["bound_times_ms"] = {"hbm": t_hbm * 1e3, "fp32": t_f32 * 1e3, "fp64": t_f64 * 1e3}
     cfg = {"workload": args.workload, "form": ["mass", "helmholtz", "elasticity", "neohookean"][form],
-           "degree": p, "elements": E, "quad_points": pl["quad_points"], "local_matrix": "%dx%d f64" % (n, n),
+           "degree": p, "elements": E, "quad_points": pl["quad_points"], "local_matrix": "%dx%d %s" % (n, n, "f32" if f32 else "f64"),
            "variant": fea.VARIANT_NAMES[pl["variant"]], "tile": pl["tile"], "geometry": "f64",
            "contraction": "f32", "parallelism": "dp%d (element shards)" % world,
            "l2": "inputs+outputs %.0f MB per step%s" % (alg_bytes / 1e6, " > 129 MB L2; no flush"
@@ -367,7 +374,7 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         "comparator": {"kernel": "plain FP64 quadrature nest", "value": naive_rate, "unit": METRIC,
                        "elements": En, "ms_per_step": ms_naive, "speedup": value / world / naive_rate},
         "e2e": {"value": E * world / (e2e_ms * 1e-3), "unit": METRIC,
-                "h2d_bytes_per_step": E * (96 + 8 * fea.coeff_len(form, p)), "d2h_bytes_per_step": E * n * n * 8,
+                "h2d_bytes_per_step": E * (96 + 8 * fea.coeff_len(form, p)), "d2h_bytes_per_step": E * n * n * esz,
                 "ms_per_step": e2e_ms},
         "gpu_launches": args.steps, "clocks": clk.summary(), "gflops": flops / (ms * 1e-3) / 1e9,
     }
@@ -398,7 +405,7 @@ def run_stream(args, fea, torch, barrier, max_over_ranks, world, local):
             b = E * pl["bytes"]
             byt += b
             tb += max(b / (hbm * 1e9), E * pl["flops_run"] / (FP32_PEAK_TFLOPS * 1e12),
-                      E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]) / (FP64_PEAK_TFLOPS * 1e12))
+                      E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]) / (FP64_PEAK_TINSTR * 1e12))
         return tb, byt
 
     def timed(steps):

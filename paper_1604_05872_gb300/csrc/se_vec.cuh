@@ -64,9 +64,9 @@ struct SeVecTile {
   static constexpr int NN = N * N;
   static constexpr int CLEN = coeff_len_c(FORM, P);
   // trial functions per thread, elements interleaved per warp, resident CTAs per SM
-  static constexpr int BB = F32 ? (P <= 2 ? 2 : P == 3 ? 4 : 3) : (P == 4 ? 3 : 2);
-  static constexpr int EF = P <= 2 ? 8 : P == 3 ? (F32 ? 4 : 2) : 1;
-  static constexpr int MINB = F32 ? (P <= 2 ? 3 : 2) : 1;
+  static constexpr int BB = P == 4 ? 3 : 2;
+  static constexpr int EF = P <= 2 ? 8 : P == 3 ? 2 : 1;
+  static constexpr int MINB = F32 ? (P <= 3 ? 3 : 2) : 1;
   using Chunks = SymChunks<NS, BB>;
   static constexpr int NCH = Chunks::NCH;
   static constexpr int GROUPS = NT / (EF * NCH);
