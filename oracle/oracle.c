@@ -491,6 +491,35 @@ int oracle_neohookean_residual(int p, int m, int64_t E, const double *coords,
   return 0;
 }
 
+/* Load vector of the Helmholtz form's right-hand side (its linear
+ * counterpart, Section 2: a form of arity 1): b_i = int f phi_i dx with f in
+ * the same P_p space as the basis, f = sum_k f_k phi_k; out is [E][n]. */
+int oracle_load_vector(int p, int m, int64_t E, const double *coords, const double *f, double *out) {
+  int n = oracle_nbasis(p);
+  int Q = oracle_rule_size(m);
+  double *X = (double *)malloc(sizeof(double) * 3 * Q);
+  double *W = (double *)malloc(sizeof(double) * Q);
+  oracle_quad_rule(m, X, W);
+  double *phi = (double *)malloc(sizeof(double) * Q * n);
+  double *dphi = (double *)malloc(sizeof(double) * Q * n * 3);
+  oracle_basis(p, Q, X, phi, dphi);
+  for (int64_t e = 0; e < E; ++e) {
+    double J[3][3], Jinv[3][3];
+    double adet = fabs(geometry(coords + 12 * e, J, Jinv));
+    const double *fe = f + (size_t)n * e;
+    double *b = out + (size_t)n * e;
+    for (int i = 0; i < n; ++i) b[i] = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      const double *ph = phi + (size_t)q * n;
+      double fq = 0.0;
+      for (int k = 0; k < n; ++k) fq += fe[k] * ph[k];
+      for (int i = 0; i < n; ++i) b[i] += W[q] * adet * fq * ph[i];
+    }
+  }
+  free(X); free(W); free(phi); free(dphi);
+  return 0;
+}
+
 /* Neo-Hookean stored energy int W(F) dx per element; out is [E]. */
 int oracle_neohookean_energy(int p, int m, int64_t E, const double *coords,
                              const double *u, double mu_c, double lam_c, double *out) {

@@ -61,6 +61,7 @@ def _load():
                                                        ctypes.c_double, ctypes.c_double, D]
             lib.oracle_neohookean_energy.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, D, D,
                                                      ctypes.c_double, ctypes.c_double, D]
+            lib.oracle_load_vector.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, D, D, D]
             _lib = lib
     return _lib
 
@@ -157,6 +158,20 @@ def neohookean_residual(p, coords, u, mu=0.8, lam=1.3, m=None):
         m = default_rule(NEOHOOKEAN, p)
     out = np.zeros((E, 3 * n))
     lib.oracle_neohookean_residual(p, m, E, _ptr(coords), _ptr(u), float(mu), float(lam), _ptr(out))
+    return out
+
+
+def load_vector(p, coords, f, m=None):
+    """Helmholtz right-hand side b_i = int f phi_i, f in P_p given by its DOFs [E, n]; [E, n]."""
+    lib = _load()
+    coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1, 12)
+    E = coords.shape[0]
+    n = nbasis(p)
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(E, n)
+    if m is None:
+        m = default_rule(HELMHOLTZ, p)
+    out = np.zeros((E, n))
+    lib.oracle_load_vector(p, m, E, _ptr(coords), _ptr(f), _ptr(out))
     return out
 
 

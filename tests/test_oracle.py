@@ -370,3 +370,45 @@ def test_neohookean_workload_keeps_det_f_positive(orc, p):
     G = np.einsum("qai,eix->eqax", dphi, Jinv)
     F = np.eye(3)[None, None] + np.einsum("eac,eqax->eqcx", u.reshape(E, -1, 3), G)
     assert np.linalg.det(F).min() > 0.05
+
+
+# ---------------------------------------------------------------- linear forms
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_load_vector_pins(orc, p):
+    """b_i = int f phi_i: constants integrate to the volume (partition of unity),
+    P1 has the closed form |K|/20 (f_i + sum_j f_j), and b = M f with the
+    (independently pinned) mass matrix, both rules being exact for degree 2p."""
+    c, rng = _mesh(5, seed=100 + p)
+    n = orc.nbasis(p)
+    vol = np.abs(np.linalg.det(np.stack([c[:, 1] - c[:, 0], c[:, 2] - c[:, 0], c[:, 3] - c[:, 0]], axis=-1))) / 6
+    b1 = orc.load_vector(p, c, np.ones((5, n)))
+    assert np.allclose(b1.sum(axis=1), vol, rtol=1e-13, atol=0)
+    f = rng.uniform(-1, 1, size=(5, n))
+    b = orc.load_vector(p, c, f)
+    M = orc.assemble(orc.MASS, p, c)
+    assert np.abs(b - np.einsum("eij,ej->ei", M, f)).max() < 1e-14 * np.abs(b).max() * n
+    if p == 1:
+        ref = vol[:, None] / 20 * (f + f.sum(axis=1, keepdims=True))
+        assert np.abs(b - ref).max() < 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_neohookean_residual_invariants(orc, p):
+    """Independent of the energy: zero and rigid-translation displacements give
+    no force; forces sum to zero per component (sum_a grad phi_a = 0); and
+    for small displacements R(eps u) = eps K_lin u + O(eps^2), K_lin the
+    linear-elasticity stiffness with the same constant mu, lambda."""
+    c, u = inputs.workload(inputs.NEOHOOKEAN, p, 3, seed=110 + p)
+    n = orc.nbasis(p)
+    assert np.abs(orc.neohookean_residual(p, c, np.zeros_like(u))).max() == 0.0
+    shift = np.tile(np.array([0.3, -0.2, 0.1]), (3, n))
+    assert np.abs(orc.neohookean_residual(p, c, shift)).max() < 1e-13
+    R = orc.neohookean_residual(p, c, u)
+    assert np.abs(R.reshape(3, n, 3).sum(axis=1)).max() < 1e-12 * np.abs(R).max()
+    co = np.concatenate([np.full((3, 4), 0.8), np.full((3, 4), 1.3)], axis=1)
+    Kl = orc.assemble(orc.ELASTICITY, p, c, co)
+    errs = []
+    for eps in (1e-2, 1e-3):
+        lin = eps * np.einsum("eij,ej->ei", Kl, u)
+        errs.append(np.linalg.norm(orc.neohookean_residual(p, c, eps * u) - lin) / np.linalg.norm(lin))
+    assert errs[1] < 0.2 * errs[0] and errs[1] < 1e-2
