@@ -236,7 +236,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="helmholtz_p2_1M", choices=sorted(WORKLOADS) + ["stream_64req_2M"])
+    ap.add_argument("--workload", default="helmholtz_p2_1M",
+                    choices=sorted(WORKLOADS) + sorted(VECTOR_WORKLOADS) + ["stream_64req_2M"])
     ap.add_argument("--elements", type=int, default=0, help="override the element count")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--tuning", default="", help="tuning JSON (records + MLP) for the stream workload")
@@ -272,6 +273,8 @@ def main():
 
     if args.workload == "stream_64req_2M":
         line = run_stream(args, fea, torch, barrier, max_over_ranks, world, local)
+    elif args.workload in VECTOR_WORKLOADS:
+        line = run_vector(args, fea, torch, barrier, max_over_ranks, world, rank, local)
     else:
         line = run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local)
     if rank == 0:
@@ -380,6 +383,89 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(form, p, coords, coeffs)
+    return line
+
+
+VECTOR_WORKLOADS = {
+    # name: (form, degree, elements) -- element vectors of the linear forms
+    "helmholtz_load_p2_1M": (1, 2, 1_000_000),
+    "neohookean_residual_p2_500k": (3, 2, 500_000),
+}
+
+
+def run_vector(args, fea, torch, barrier, max_over_ranks, world, rank, local):
+    """Element vectors (fea_assemble_vector): the Helmholtz load vector or the
+    Neo-Hookean residual of the matrix workloads' inputs."""
+    from paper_1604_05872_gb300 import inputs
+    form, p, E0 = VECTOR_WORKLOADS[args.workload]
+    E = args.elements or E0
+    coords, coeffs = inputs.workload(form, p, E, seed=inputs.SEED + rank)
+    c = torch.from_numpy(coords).cuda()
+    fc = torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
+    f32 = bool(args.out_f32)
+    n = fea.local_dim(form, p)
+    out = torch.empty((E, n), dtype=torch.float32 if f32 else torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        fea.assemble_vector(form, p, c, fc, out=out, out_f32=f32)
+    fea.sync()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fea.assemble_vector(form, p, c, fc, out=out, out_f32=f32)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    fea.sync()
+    ms_max = max_over_ranks(ms)
+    ns = (p + 1) * (p + 2) * (p + 3) // 6
+    Q = fea.quad_points(form if form == 3 else 0, p)
+    esz = 4 if f32 else 8
+    bytes_elem = 96 + 8 * fea.coeff_len(form, p) + esz * n
+    # executed FP32 flops and FP64 lane-instructions per element (estimates of the kernels' loop nests)
+    if form == 1:
+        flops, f64 = 2 * ns * ns + ns, 20
+    else:
+        flops, f64 = Q * (2 * 9 * ns + 2 * 27 + 2 * 27 + 2 * 27 + 18 * ns), 50 + 41 * Q
+    hbm, peak_kind = peaks()
+    alg_bytes, fl, f64t = E * bytes_elem, E * flops, E * f64
+    t_hbm, t_f32, t_f64 = alg_bytes / (hbm * 1e9), fl / (FP32_PEAK_TFLOPS * 1e12), f64t / (FP64_PEAK_TINSTR * 1e12)
+    if t_hbm >= max(t_f32, t_f64):
+        roof = {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_kind": peak_kind}
+    elif t_f64 >= t_f32:
+        roof = {"bound": "alu", "achieved": f64t / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TINSTR,
+                "unit": "T FP64 lane-instructions/s", "peak_kind": "derived: FP64 lanes x clock"}
+    else:
+        roof = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_kind": "derived: FP32 lanes x clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["alg_bytes_per_launch"] = alg_bytes
+    roof["bound_times_ms"] = {"hbm": t_hbm * 1e3, "fp32": t_f32 * 1e3, "fp64": t_f64 * 1e3}
+    line = {
+        "metric": "element vectors/s", "value": E * world / (ms_max * 1e-3), "unit": "element vectors/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "form": ["mass", "helmholtz", "elasticity", "neohookean"][form],
+                   "degree": p, "elements": E, "quad_points": Q, "local_vector": "%d %s" % (n, "f32" if f32 else "f64"),
+                   "l2": "inputs+outputs %.0f MB per step%s" % (alg_bytes / 1e6, " > 129 MB L2; no flush"
+                                                             if alg_bytes > 129e6 else " (fits L2)")},
+        "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(), "e2e": None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        nsamp = min(E, 1_000_000 if form == 1 else 50_000)
+        t0 = time.perf_counter()
+        if form == 1:
+            oracle.load_vector(p, coords[:nsamp], coeffs[:nsamp])
+        else:
+            oracle.neohookean_residual(p, coords[:nsamp], coeffs[:nsamp])
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nsamp / dt, "unit": "element vectors/s", "cores": 1, "kind": "oracle",
+                                "sample": "first %d elements, FP64 loop nest, one core, %.2f s" % (nsamp, dt)}
     return line
 
 

@@ -138,6 +138,22 @@ int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host
                       const double* coeffs_host, void* out_host, const fea_options* opt,
                       void* stream);
 
+/* Element VECTORS of the linear forms (arity 1, Section 2), E of them, on
+ * `stream` (device pointers, 16-byte aligned):
+ *   FEA_HELMHOLTZ:   the load vector b_i = int f phi_i, f in P_degree given by
+ *                    its DOFs; coeffs as for the Helmholtz matrix ([E][n_p]);
+ *                    out [E][n_p].
+ *   FEA_NEOHOOKEAN:  the residual R_(a,c) = int P(F)_{cx} dphi_a/dx_x with
+ *                    P = mu (F - F^-T) + lam ln det F F^-T; coeffs as for the
+ *                    tangent ([E][n_p][3] displacements, then mu, lam);
+ *                    out [E][3 n_p], index 3 a + c.
+ * Other forms return FEA_EINVAL.  opt: precision (FP32 contraction with FP64
+ * geometry and FP64 det F / ln det F, or FP64), out_f32, tile (0 = default),
+ * smem_budget; variant must be AUTO.  Degenerate elements give NaN entries
+ * and FEA_EDEGENERATE at the next fea_sync. */
+int fea_assemble_vector(int form, int degree, int64_t E, const double* coords,
+                        const double* coeffs, void* out, const fea_options* opt, void* stream);
+
 /* Uneven batch of requests in one persistent launch (captured once into a CUDA
  * graph per distinct batch shape and replayed).  Tiles are pulled from a work
  * list with an atomic counter; all requests use the same options. */

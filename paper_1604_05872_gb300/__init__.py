@@ -23,6 +23,7 @@ VARIANT_AUTO, VARIANT_NAIVE, VARIANT_SE, VARIANT_PRE = -1, 0, 1, 2
 VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
+           "fea_assemble_vector",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_noalloc",
            "fea_sync", "fea_plan", "fea_plan_flop",
            "fea_op_count", "fea_opcount_program", "fea_sharing_elimination", "fea_vertex_cover",
@@ -78,6 +79,7 @@ def load(path=None):
     lib.fea_assemble_ex.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_host.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_batch.argtypes = [P(Request), i, P(Options), vp]
+    lib.fea_assemble_vector.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
@@ -177,6 +179,23 @@ def assemble_host(form, degree, coords, coeffs, out, precision=PREC_FP32, out_f3
     o = options(precision, out_f32, variant, tile, 0)
     _check(load().fea_assemble_host(form, degree, coords.shape[0], _ptr(coords), _ptr(coeffs), _ptr(out),
                                     ctypes.byref(o), _stream_ptr(stream)))
+    return out
+
+
+def assemble_vector(form, degree, coords, coeffs, out=None, precision=PREC_FP32, out_f32=False, tile=0,
+                    smem_budget=0, stream=None):
+    """Element vectors of the linear forms (fea_assemble_vector): the Helmholtz
+    load vector [E, n_p] or the Neo-Hookean residual [E, 3 n_p]; returns `out`."""
+    import torch
+    E = coords.shape[0]
+    n = local_dim(form, degree)
+    if n < 0:
+        raise FeaError(1, "unsupported form/degree")
+    if out is None:
+        out = torch.empty((E, n), dtype=torch.float32 if out_f32 else torch.float64, device=coords.device)
+    o = options(precision, out_f32, VARIANT_AUTO, tile, smem_budget)
+    _check(load().fea_assemble_vector(form, degree, E, _ptr(coords), _ptr(coeffs), _ptr(out), ctypes.byref(o),
+                                      _stream_ptr(stream)))
     return out
 
 

@@ -293,6 +293,43 @@ int assemble_impl(int form, int degree, int64_t E, const double* coords, const d
   return launch_plan(st, pl, form, degree, E, coords, coeffs, out, o.out_f32, (cudaStream_t)stream);
 }
 
+// Element vectors (linear forms): Helmholtz load vector, Neo-Hookean residual.
+int assemble_vector_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
+                         const fea_options* opt, void* stream) {
+  if (!valid_fd(form, degree)) return fail(FEA_EINVAL, "unsupported form/degree");
+  if (form != FEA_HELMHOLTZ && form != FEA_NEOHOOKEAN)
+    return fail(FEA_EINVAL, "element vectors exist for the Helmholtz load vector and the Neo-Hookean residual only");
+  if (E < 0) return fail(FEA_EINVAL, "negative element count");
+  const fea_options o = opt ? *opt : default_options();
+  if (o.out_f32 != 0 && o.out_f32 != 1) return fail(FEA_EINVAL, "out_f32 must be 0 or 1");
+  if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32) return fail(FEA_EINVAL, "unsupported precision");
+  if (o.variant != FEA_VARIANT_AUTO) return fail(FEA_EINVAL, "element vectors have one variant (AUTO)");
+  DevState* st = nullptr;
+  int rc = get_dev(&st);
+  if (rc) return rc;
+  const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
+  // the load vector reads the mass form's pre-evaluated table (int phi_i phi_k)
+  const int table_form = form == FEA_HELMHOLTZ ? FEA_MASS : form;
+  Plan pl;
+  pl.k = find_vec_kernel(form, degree, prec);
+  if (!pl.k) return fail(FEA_EINVAL, "no element-vector kernel for this form/degree/precision");
+  pl.variant = pl.k->variant;
+  pl.prec = prec;
+  pl.Q = rule_points(rule_index(table_form, degree));
+  const size_t limit = st->smem_optin;
+  const size_t budget = o.smem_budget ? std::min(o.smem_budget, limit) : limit;
+  pl.tile = o.tile ? o.tile : pl.k->pref_tile;
+  if (pl.tile < 1 || pl.tile > pl.k->max_tile) return fail(FEA_EINVAL, "tile out of range for this kernel");
+  while (o.tile == 0 && pl.tile > 1 && pl.k->smem(pl.tile, pl.Q) > budget) --pl.tile;
+  pl.smem = pl.k->smem(pl.tile, pl.Q);
+  if (pl.smem > budget) return fail(FEA_EINVAL, "tile does not fit the shared-memory budget (Constraint 2)");
+  if (E == 0) return FEA_OK;
+  if ((rc = check_device_ptr(coords, "coords", false))) return rc;
+  if ((rc = check_device_ptr(coeffs, "coeffs", false))) return rc;
+  if ((rc = check_device_ptr(out, "out", false))) return rc;
+  return launch_plan(st, pl, table_form, degree, E, coords, coeffs, out, o.out_f32, (cudaStream_t)stream);
+}
+
 // ------------------------------------------------------------------ host API
 static int ensure_ws(DevState* st, int b, int k, size_t bytes) {
   if (st->ws_bytes[b][k] >= bytes) return FEA_OK;
@@ -431,6 +468,10 @@ int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host
 }
 int fea_assemble_batch(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   return batch_impl(reqs, nreq, opt, stream);
+}
+int fea_assemble_vector(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
+                        const fea_options* opt, void* stream) {
+  return assemble_vector_impl(form, degree, E, coords, coeffs, out, opt, stream);
 }
 int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   return batch_noalloc_impl(reqs, nreq, opt, stream);

@@ -31,5 +31,7 @@ extern const int kNumPreTileF32;
 const KernelInfo* find_kernel(int variant, int form, int p, int prec, size_t budget = 0, int Q = 0);
 // Tile functions of the batched persistent kernel (FP32): PreTile / SeTile.
 const KernelInfo* find_batch_kernel(int variant, int form, int p);
+// Element-vector kernels (linear forms): Helmholtz load vector, Neo-Hookean residual.
+const KernelInfo* find_vec_kernel(int form, int p, int prec);
 
 }  // namespace fea
