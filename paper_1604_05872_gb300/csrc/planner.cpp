@@ -190,6 +190,9 @@ int default_tile(int variant, int form, int p, int prec, int max_tile, size_t bu
   int best = 1;
   for (int te = 1; te <= max_tile; ++te)
     if (smem(te, Q) <= target) best = te;
+  // whole warps for the per-element FP64 geometry (one lane per element): an
+  // FP64 instruction holds the FP64 unit for the full warp whatever its lanes
+  if (best >= 32) best = best / 32 * 32;
   (void)variant;
   return best;
 }

@@ -34,7 +34,8 @@ struct LoadVecTile {
   FEA_HD static int max_tile() { return TE; }
   FEA_HD static int pref_tile() { return TE; }
   FEA_HD static size_t off_f(int te) { return round_up_sz((size_t)te * 12 * 8, 16); }
-  FEA_HD static size_t off_m(int te) { return off_f(te) + round_up_sz((size_t)te * NS * 8, 16); }
+  FEA_HD static size_t off_ft(int te) { return off_f(te) + round_up_sz((size_t)te * NS * 8, 16); }
+  FEA_HD static size_t off_m(int te) { return off_ft(te) + round_up_sz((size_t)te * NS * sizeof(T), 16); }
   FEA_HD static size_t off_det(int te) { return off_m(te) + round_up_sz((size_t)NS * NS * sizeof(T), 16); }
   FEA_HD static size_t smem(int te, int Q) { (void)Q; return off_det(te) + round_up_sz((size_t)te * sizeof(T), 16); }
 
@@ -42,6 +43,7 @@ struct LoadVecTile {
     const int te = q.tile;
     double* xs = reinterpret_cast<double*>(sm);
     double* fs = reinterpret_cast<double*>(sm + off_f(te));
+    T* ft = reinterpret_cast<T*>(sm + off_ft(te));
     T* M = reinterpret_cast<T*>(sm + off_m(te));
     T* adet = reinterpret_cast<T*>(sm + off_det(te));
     const TabLayout L = tab_layout(q.Q, NS, 1);
@@ -65,14 +67,15 @@ struct LoadVecTile {
       if (bad) flag_error(err, ERR_DEGENERATE);
       adet[tid] = bad ? T(__int_as_float(0x7fc00000)) : from_double<T>(fabs(det));
     }
+    for (int k = tid; k < ne * NS; k += NT) ft[k] = from_double<T>(fs[k]);  // each DOF converted once
     __syncthreads();
     for (int w = tid; w < ne * NS; w += NT) {
       const int e = w / NS, i = w - e * NS;
-      const double* f = fs + NS * e;
+      const T* f = ft + NS * e;
       const T* m = M + NS * i;
       T acc = T(0);
 #pragma unroll 5
-      for (int k = 0; k < NS; ++k) acc = fma(m[k], from_double<T>(f[k]), acc);
+      for (int k = 0; k < NS; ++k) acc = fma(m[k], f[k], acc);
       put_out<T>(q.out, e0 * NS + w, adet[e] * acc, q.out_f32);
     }
     __syncthreads();
