@@ -96,6 +96,21 @@ def test_float_output_and_default_call(fea, orc):
     assert torch.equal(o64.float(), o32)
 
 
+@pytest.mark.parametrize("form,p", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 3), (2, 1), (2, 2), (2, 3), (3, 2)])
+def test_float_output_every_streaming_kernel(fea, orc, form, p):
+    """FP32 output equals the FP64 output rounded (both come from the same FP32
+    contraction), on ragged sizes, for the kernels with their own FP32 store path."""
+    E = 777
+    coords, coeffs = inputs.workload(form, p, E, seed=40 + 4 * form + p)
+    c, f = to_dev(coords, coeffs, form, p)
+    o32 = fea.assemble(form, p, c, f, out_f32=True)
+    o64 = fea.assemble(form, p, c, f)
+    fea.sync()
+    assert torch.equal(o64.float(), o32)
+    ref = oracle_ref(orc, form, p, coords, coeffs)
+    assert orc.rel_frobenius(o32.double().cpu().numpy(), ref).max() <= 1e-5
+
+
 def test_host_buffer_call_equals_device_call(fea):
     for form, p in [(1, 2), (3, 2), (2, 3)]:
         E = 777
