@@ -14,18 +14,18 @@ KernelInfo stream_info() {
   return KernelInfo{reinterpret_cast<const void*>(&pre_stream_kernel<F, P>), V_PRE, F, P, 1, NT, &stream_smem<F, P>, 0};
 }
 
-template <int P>
-size_t vstream_smem(int TE, int Q) { return PreVecStream<P>::smem(TE, Q); }
-template <int P>
-KernelInfo vstream_info() {
-  return KernelInfo{reinterpret_cast<const void*>(&pre_vec_stream_kernel<P>), V_PRE, 2, P, 1, PreVecStream<P>::TE,
-                    &vstream_smem<P>, PreVecStream<P>::TE};
+template <class Pol>
+size_t batched_smem(int TE, int Q) { return StreamLayout<Pol>::smem(TE, Q); }
+template <class Pol>
+KernelInfo batched_info(int variant, int form, int p) {
+  return KernelInfo{reinterpret_cast<const void*>(&stream_batched_kernel<Pol>), variant, form, p, 1, Pol::TE,
+                    &batched_smem<Pol>, Pol::TE};
 }
 
 #define PRE(F, P) make_info<PreTile<F, P, float>>(V_PRE, F, P, 1), make_info<PreTile<F, P, double>>(V_PRE, F, P, 0)
 #define PRES(F, P) stream_info<F, P>(), make_info<PreTile<F, P, double>>(V_PRE, F, P, 0)
 #define PREV(P) make_info<PreVecTile<P, float>>(V_PRE, 2, P, 1), make_info<PreVecTile<P, double>>(V_PRE, 2, P, 0)
-#define PREVS(P) vstream_info<P>(), make_info<PreVecTile<P, float>>(V_PRE, 2, P, 1), make_info<PreVecTile<P, double>>(V_PRE, 2, P, 0)
+#define PREVS(P) batched_info<VecStreamPolicy<P>>(V_PRE, 2, P), make_info<PreVecTile<P, float>>(V_PRE, 2, P, 1), make_info<PreVecTile<P, double>>(V_PRE, 2, P, 0)
 const KernelInfo kPreKernels[] = {
     PRES(0, 1), PRES(0, 2), PRES(0, 3), PRE(0, 4),
     PRES(1, 1), PRES(1, 2), PRES(1, 3), PRE(1, 4),
