@@ -154,10 +154,19 @@ int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host
 int fea_assemble_vector(int form, int degree, int64_t E, const double* coords,
                         const double* coeffs, void* out, const fea_options* opt, void* stream);
 
-/* Uneven batch of requests in one persistent launch (captured once into a CUDA
- * graph per distinct batch shape and replayed).  Tiles are pulled from a work
- * list with an atomic counter; all requests use the same options. */
+/* Uneven batch of requests (forms, degrees and sizes mixed) in one CUDA graph
+ * launch, captured once per distinct batch and replayed: each request runs the
+ * persistent kernel it would run alone (its own tile, registers and shared
+ * memory), the requests spread over concurrent graph branches, largest first.
+ * All requests use the same options (FP32 contraction). */
 int fea_assemble_batch(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
+
+/* The same batch as ONE persistent kernel launch (also graph-captured): the
+ * tiles of all requests form a work list that CTAs pull with an atomic
+ * counter, dispatching on (variant, form, degree) to the FP32 tile functions;
+ * one register and shared-memory budget serves every request.  Same results
+ * as fea_assemble_batch. */
+int fea_assemble_batch_fused(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
 
 /* The batched launch above, for callers that cannot allocate device memory at
  * the moment they assemble: code that runs while a CUDA graph is being

@@ -24,7 +24,8 @@ VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
            "fea_assemble_vector",
-           "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_noalloc",
+           "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_fused",
+           "fea_assemble_batch_noalloc",
            "fea_sync", "fea_plan", "fea_plan_flop",
            "fea_op_count", "fea_opcount_program", "fea_sharing_elimination", "fea_vertex_cover",
            "fea_increase_factor", "fea_num_monomials", "fea_theta", "fea_algorithm3",
@@ -79,6 +80,7 @@ def load(path=None):
     lib.fea_assemble_ex.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_host.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_batch.argtypes = [P(Request), i, P(Options), vp]
+    lib.fea_assemble_batch_fused.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_assemble_vector.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
@@ -199,14 +201,17 @@ def assemble_vector(form, degree, coords, coeffs, out=None, precision=PREC_FP32,
     return out
 
 
-def assemble_batch(requests, out_f32=False, stream=None):
-    """requests: list of (form, degree, coords, coeffs, out) device tensors, one persistent launch."""
+def assemble_batch(requests, out_f32=False, stream=None, fused=False):
+    """requests: list of (form, degree, coords, coeffs, out) device tensors, one CUDA graph launch
+    (fea_assemble_batch: one persistent kernel per request; fused=True: fea_assemble_batch_fused,
+    one persistent kernel over a work list of all requests' tiles)."""
     arr = (Request * len(requests))()
     for k, (form, degree, coords, coeffs, out) in enumerate(requests):
         arr[k] = Request(form, degree, coords.shape[0], coords.data_ptr(),
                          None if coeffs is None else coeffs.data_ptr(), out.data_ptr())
     o = options(PREC_FP32, out_f32)
-    _check(load().fea_assemble_batch(arr, len(requests), ctypes.byref(o), _stream_ptr(stream)))
+    fn = load().fea_assemble_batch_fused if fused else load().fea_assemble_batch
+    _check(fn(arr, len(requests), ctypes.byref(o), _stream_ptr(stream)))
 
 
 def assemble_batch_noalloc(requests, out_f32=False, stream=None):

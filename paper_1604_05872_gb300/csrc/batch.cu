@@ -85,7 +85,10 @@ __global__ void __launch_bounds__(NT, 2) batch_kernel(const Req* __restrict__ re
   }
 }
 
+constexpr int kBranches = 4;  // concurrent branches of the per-request graph
+
 struct BatchState {
+  // one fused persistent kernel (fea_assemble_batch_fused)
   std::vector<Req> sig;  // requests of the captured graph
   size_t smem = 0;
   int grid = 0;
@@ -94,12 +97,22 @@ struct BatchState {
   unsigned long long* counter = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // one persistent kernel per request in concurrent graph branches (fea_assemble_batch)
+  std::vector<PreparedLaunch> gsig;
+  cudaGraph_t ggraph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t br[kBranches] = {};
+  cudaEvent_t ev[kBranches + 1] = {};
 };
 
 void free_batch_state(BatchState* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->ggraph) cudaGraphDestroy(b->ggraph);
+  for (auto& x : b->br) if (x) cudaStreamDestroy(x);
+  for (auto& x : b->ev) if (x) cudaEventDestroy(x);
   if (b->dreqs) cudaFree(b->dreqs);
   if (b->counter) cudaFree(b->counter);
   delete b;
@@ -116,13 +129,15 @@ const void* table_ptr(DevState* st, int form, int p, int prec, int* rc);
 int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch);
 int set_error(int code, const char* msg);
 int check_device_ptr(const void* p, const char* what, bool allow_null);
+int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, const double* coords,
+                   const double* coeffs, void* out, int out_f32, PreparedLaunch* L);
 
 static bool same_sig(const std::vector<Req>& a, const std::vector<Req>& b) {
   if (a.size() != b.size()) return false;
   return a.empty() || std::memcmp(a.data(), b.data(), a.size() * sizeof(Req)) == 0;
 }
 
-int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
+int batch_fused_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   if (nreq < 0 || (nreq > 0 && !reqs)) return set_error(FEA_EINVAL, "bad request list");
   if (nreq == 0) return FEA_OK;
   fea_options o;
@@ -218,6 +233,99 @@ int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* 
     bs->sig = R;
   }
   if ((e = cudaGraphLaunch(bs->exec, s)) != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  return FEA_OK;
+}
+
+// ------------------------------------------------------------------------
+// The default batch schedule: one CUDA graph whose nodes are the requests' own
+// standalone persistent kernels (each with its own tile, registers and shared
+// memory), spread over concurrent branches, largest requests first.  Captured
+// once per distinct batch and replayed.
+// ------------------------------------------------------------------------
+static bool same_launches(const std::vector<PreparedLaunch>& a, const std::vector<PreparedLaunch>& b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i)
+    if (a[i].fn != b[i].fn || a[i].grid != b[i].grid || a[i].smem != b[i].smem || a[i].err != b[i].err ||
+        std::memcmp(&a[i].q, &b[i].q, sizeof(Req)) != 0)
+      return false;
+  return true;
+}
+
+int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
+  if (nreq < 0 || (nreq > 0 && !reqs)) return set_error(FEA_EINVAL, "bad request list");
+  if (nreq == 0) return FEA_OK;
+  fea_options o;
+  if (opt) o = *opt;
+  else { o.precision = FEA_PREC_FP32; o.out_f32 = 0; o.variant = FEA_VARIANT_AUTO; o.tile = 0; o.smem_budget = 0; }
+  if (o.precision != FEA_PREC_FP32) return set_error(FEA_EINVAL, "the batched launch runs the FP32 contraction");
+  DevState* st = nullptr;
+  int rc = get_dev_state(&st);
+  if (rc) return rc;
+  std::vector<std::pair<double, PreparedLaunch>> work;
+  work.reserve(nreq);
+  for (int i = 0; i < nreq; ++i) {
+    const fea_request& r = reqs[i];
+    if (r.form < 0 || r.form > 3 || r.degree < 1 || r.degree > 4 || r.E < 0)
+      return set_error(FEA_EINVAL, "bad request");
+    if (r.E == 0) continue;
+    if ((rc = check_device_ptr(r.coords, "coords", false))) return rc;
+    if ((rc = check_device_ptr(r.coeffs, "coeffs", r.form == FEA_MASS))) return rc;
+    if ((rc = check_device_ptr(r.out, "out", false))) return rc;
+    Plan pl;
+    if ((rc = make_plan(st, r.form, r.degree, o, &pl, false))) return rc;
+    if (pl.variant == FEA_VARIANT_NAIVE) return set_error(FEA_EINVAL, "the batched launch has no plain variant");
+    PreparedLaunch L;
+    if ((rc = prepare_launch(st, pl, r.form, r.degree, r.E, r.coords, r.coeffs, r.out, o.out_f32, &L))) return rc;
+    const int n = (r.form >= 2 ? 3 : 1) * (r.degree + 1) * (r.degree + 2) * (r.degree + 3) / 6;
+    work.emplace_back((double)r.E * n * n, L);  // output size: the larger requests first
+  }
+  if (work.empty()) return FEA_OK;
+  std::stable_sort(work.begin(), work.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<PreparedLaunch> L;
+  L.reserve(work.size());
+  for (auto& w : work) L.push_back(w.second);
+  BatchState*& bs = dev_batch(st);
+  if (!bs) bs = new BatchState();
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!bs->gexec || !same_launches(bs->gsig, L)) {
+    if (bs->gexec) { cudaGraphExecDestroy(bs->gexec); bs->gexec = nullptr; }
+    if (bs->ggraph) { cudaGraphDestroy(bs->ggraph); bs->ggraph = nullptr; }
+    for (auto& x : bs->br)
+      if (!x && (e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking)) != cudaSuccess)
+        return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    for (auto& x : bs->ev)
+      if (!x && (e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess)
+        return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    // capture: fork from branch 0 into the others, one kernel per request on the
+    // least-loaded branch, join back into branch 0
+    double load[kBranches] = {};
+    e = cudaStreamBeginCapture(bs->br[0], cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(bs->ev[kBranches], bs->br[0]);
+    for (int k = 1; k < kBranches && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(bs->br[k], bs->ev[kBranches], 0);
+    for (size_t i = 0; i < L.size() && e == cudaSuccess; ++i) {
+      int k = 0;
+      for (int b = 1; b < kBranches; ++b)
+        if (load[b] < load[k]) k = b;
+      load[k] += work[i].first;
+      void* args[] = {&L[i].q, &L[i].err};
+      e = cudaLaunchKernel(L[i].fn, dim3(L[i].grid), dim3(NT), args, L[i].smem, bs->br[k]);
+    }
+    for (int k = 1; k < kBranches && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(bs->ev[k], bs->br[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(bs->br[0], bs->ev[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(bs->br[0], &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return set_error(FEA_ECUDA, cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    bs->ggraph = g;
+    if ((e = cudaGraphInstantiate(&bs->gexec, g, 0)) != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    bs->gsig = L;
+  }
+  if ((e = cudaGraphLaunch(bs->gexec, s)) != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
   return FEA_OK;
 }
 

@@ -224,8 +224,11 @@ int check_device_ptr(const void* p, const char* what, bool allow_null) {
   return FEA_OK;
 }
 
-int launch_plan(DevState* st, const Plan& pl, int form, int p, int64_t E, const double* coords, const double* coeffs,
-                void* out, int out_f32, cudaStream_t stream) {
+// Everything a launch of plan `pl` needs, resolved on the host: tables resident,
+// the kernel's shared-memory ceiling raised, the persistent grid sized from
+// its occupancy.  No stream work (usable before a graph capture).
+int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, const double* coords,
+                   const double* coeffs, void* out, int out_f32, PreparedLaunch* L) {
   TableEntry* te = nullptr;
   int rc = get_tables(st, form, p, pl.prec, &te);
   if (rc) return rc;
@@ -265,11 +268,26 @@ int launch_plan(DevState* st, const Plan& pl, int form, int p, int64_t E, const 
     }
   }
   if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with this tile");
-  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
-  unsigned* err = st->err;
-  void* args[] = {&q, &err};
-  CUDA_TRY(cudaLaunchKernel(pl.k->fn, dim3((unsigned)grid), dim3(NT), args, pl.smem, stream));
+  L->fn = pl.k->fn;
+  L->grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
+  L->smem = pl.smem;
+  L->q = q;
+  L->err = st->err;
   return FEA_OK;
+}
+
+int issue_launch(PreparedLaunch& L, cudaStream_t stream) {
+  void* args[] = {&L.q, &L.err};
+  CUDA_TRY(cudaLaunchKernel(L.fn, dim3(L.grid), dim3(NT), args, L.smem, stream));
+  return FEA_OK;
+}
+
+int launch_plan(DevState* st, const Plan& pl, int form, int p, int64_t E, const double* coords, const double* coeffs,
+                void* out, int out_f32, cudaStream_t stream) {
+  PreparedLaunch L;
+  int rc = prepare_launch(st, pl, form, p, E, coords, coeffs, out, out_f32, &L);
+  if (rc) return rc;
+  return issue_launch(L, stream);
 }
 
 int assemble_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
@@ -437,6 +455,7 @@ void finalize_impl() {
 }
 
 int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
+int batch_fused_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
 int batch_noalloc_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
 
 }  // namespace fea
@@ -472,6 +491,9 @@ int fea_assemble_batch(const fea_request* reqs, int nreq, const fea_options* opt
 int fea_assemble_vector(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
                         const fea_options* opt, void* stream) {
   return assemble_vector_impl(form, degree, E, coords, coeffs, out, opt, stream);
+}
+int fea_assemble_batch_fused(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
+  return batch_fused_impl(reqs, nreq, opt, stream);
 }
 int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   return batch_noalloc_impl(reqs, nreq, opt, stream);

@@ -15,6 +15,15 @@ struct Plan {
   size_t smem = 0;
 };
 
+// A launch resolved on the host (kernel, persistent grid, shared memory, request).
+struct PreparedLaunch {
+  const void* fn = nullptr;
+  unsigned grid = 0;
+  size_t smem = 0;
+  Req q{};
+  unsigned* err = nullptr;
+};
+
 // Per-element operation counts (adds and products; an FMA counts 2) of the
 // three loop nests as the kernels execute them.  pre = -1 when the form has no
 // pre-evaluated form.

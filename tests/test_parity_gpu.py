@@ -167,15 +167,16 @@ def test_degenerate_element_flags_and_writes_nan(fea):
     fea.sync()  # cleared
 
 
-def test_batch_matches_standalone(fea, orc):
+@pytest.mark.parametrize("fused", [False, True])
+def test_batch_matches_standalone(fea, orc, fused):
     reqs = [(0, 1, 50), (1, 2, 333), (2, 3, 17), (3, 2, 41), (1, 4, 9), (2, 2, 120), (3, 1, 64), (0, 4, 11)]
     built = []
     for k, (form, p, E) in enumerate(reqs):
         coords, coeffs = inputs.workload(form, p, E, seed=50 + k)
         c, f = to_dev(coords, coeffs, form, p)
         built.append((form, p, c, f, fea.empty_out(form, p, E), coords, coeffs))
-    fea.assemble_batch([(form, p, c, f, o) for (form, p, c, f, o, _, _) in built])
-    fea.assemble_batch([(form, p, c, f, o) for (form, p, c, f, o, _, _) in built])  # graph replay
+    fea.assemble_batch([(form, p, c, f, o) for (form, p, c, f, o, _, _) in built], fused=fused)
+    fea.assemble_batch([(form, p, c, f, o) for (form, p, c, f, o, _, _) in built], fused=fused)  # graph replay
     fea.sync()
     for (form, p, c, f, o, coords, coeffs) in built:
         single = fea.assemble(form, p, c, f)
