@@ -44,7 +44,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ["common.cuh", "layout.h", "pre_stream.cuh"]  # what the timed kernel is built from
+KERNEL_SOURCES = ["common.cuh", "layout.h", "pre_stream.cuh", "planner.cpp"]  # the timed kernel and its tile rule
 
 
 def kernel_source_hash():
@@ -240,7 +240,8 @@ def main():
                     choices=sorted(WORKLOADS) + sorted(VECTOR_WORKLOADS) + ["stream_64req_2M"])
     ap.add_argument("--elements", type=int, default=0, help="override the element count")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--tuning", default="", help="tuning JSON (records + MLP) for the stream workload")
+    ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_1604_05872_gb300", "data", "tuning_gb300.json"),
+                    help="tuning JSON (records + MLP) for the stream workload ('' for the flop-count choice only)")
     ap.add_argument("--out-f32", action="store_true", help="FP32 output (element matrices stored as float)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
