@@ -154,6 +154,30 @@ int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host
 int fea_assemble_vector(int form, int degree, int64_t E, const double* coords,
                         const double* coeffs, void* out, const fea_options* opt, void* stream);
 
+/* Global assembly (the sum over elements of the element matrices at their
+ * global degrees of freedom).
+ *
+ * fea_csr_pattern (HOST arrays): the CSR sparsity pattern of a mesh whose
+ * element e has global DOFs dofs[e][0..n) (int32, row-major [E][n]; vector
+ * forms number DOF 3 a + c of a node a as the caller's global map says), with
+ * sorted unique columns per row.  Two calls: first with col_idx = NULL to get
+ * *nnz (row_ptr may be NULL too), then with row_ptr [nrows + 1] and col_idx
+ * [*nnz] to fill them.  FEA_EINVAL for a DOF outside [0, nrows) or a col_idx
+ * smaller than *nnz.
+ *
+ * fea_scatter_add_csr (DEVICE arrays, on `stream`): values[k] += elem[e][i][j]
+ * for k the position of column dofs[e][j] in row dofs[e][i]; elem is [E][n][n]
+ * double (elem_f32 = 0) or float (1), as fea_assemble writes it; values is
+ * [nnz] double and is accumulated into (zero it first for a fresh matrix).
+ * FP64 atomics: the sum order, and so the last bits, vary between runs.  A DOF,
+ * row segment or column outside the pattern is skipped and makes the next
+ * fea_sync return FEA_EINVAL. */
+int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nrows, int64_t* row_ptr,
+                    int32_t* col_idx, int64_t* nnz);
+int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const void* elem, int elem_f32,
+                        int64_t nrows, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz,
+                        double* values, void* stream);
+
 /* Uneven batch of requests (forms, degrees and sizes mixed) in one CUDA graph
  * launch, captured once per distinct batch and replayed: each request runs the
  * persistent kernel it would run alone (its own tile, registers and shared

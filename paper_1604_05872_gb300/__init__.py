@@ -23,7 +23,7 @@ VARIANT_AUTO, VARIANT_NAIVE, VARIANT_SE, VARIANT_PRE = -1, 0, 1, 2
 VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
-           "fea_assemble_vector",
+           "fea_assemble_vector", "fea_csr_pattern", "fea_scatter_add_csr",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_fused",
            "fea_assemble_batch_noalloc",
            "fea_sync", "fea_plan", "fea_plan_flop",
@@ -82,6 +82,8 @@ def load(path=None):
     lib.fea_assemble_batch.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_assemble_batch_fused.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_assemble_vector.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
+    lib.fea_csr_pattern.argtypes = [i64, i, vp, i64, vp, vp, P(i64)]
+    lib.fea_scatter_add_csr.argtypes = [i64, i, vp, vp, i, i64, vp, vp, i64, vp, vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
@@ -199,6 +201,33 @@ def assemble_vector(form, degree, coords, coeffs, out=None, precision=PREC_FP32,
     _check(load().fea_assemble_vector(form, degree, E, _ptr(coords), _ptr(coeffs), _ptr(out), ctypes.byref(o),
                                       _stream_ptr(stream)))
     return out
+
+
+def csr_pattern(dofs, nrows):
+    """CSR pattern (row_ptr int64 [nrows + 1], col_idx int32 [nnz]) of the element-to-DOF map
+    `dofs` (host int32 array [E, n]); fea_csr_pattern, built on the host."""
+    import numpy as np
+    d = np.ascontiguousarray(dofs, dtype=np.int32)
+    E, n = d.shape
+    nnz = ctypes.c_int64(0)
+    _check(load().fea_csr_pattern(E, n, d.ctypes.data, nrows, None, None, ctypes.byref(nnz)))
+    row_ptr = np.empty(nrows + 1, dtype=np.int64)
+    col_idx = np.empty(max(1, nnz.value), dtype=np.int32)
+    _check(load().fea_csr_pattern(E, n, d.ctypes.data, nrows, row_ptr.ctypes.data, col_idx.ctypes.data,
+                                  ctypes.byref(nnz)))
+    return row_ptr, col_idx[:nnz.value]
+
+
+def scatter_add_csr(dofs, elem, row_ptr, col_idx, values, stream=None):
+    """values += the element matrices `elem` [E, n, n] (device, double or float) at the global DOFs
+    `dofs` [E, n] (device int32) of the CSR pattern (row_ptr int64, col_idx int32, values double;
+    device); fea_scatter_add_csr.  Returns `values`."""
+    import torch
+    E, n = dofs.shape
+    f32 = elem.dtype == torch.float32
+    _check(load().fea_scatter_add_csr(E, n, _ptr(dofs), _ptr(elem), int(f32), row_ptr.shape[0] - 1, _ptr(row_ptr),
+                                      _ptr(col_idx), col_idx.shape[0], _ptr(values), _stream_ptr(stream)))
+    return values
 
 
 def assemble_batch(requests, out_f32=False, stream=None, fused=False):

@@ -428,6 +428,7 @@ int sync_impl(void* stream) {
   if (h) {
     CUDA_TRY(cudaMemset(st->err, 0, sizeof(unsigned)));
     if (h & 4u) return fail(FEA_EINVAL, "a kernel refused a tile larger than its shared memory");
+    if (h & 8u) return fail(FEA_EINVAL, "global assembly: a DOF, row segment or column is outside the CSR pattern");
     if (h & 2u) return fail(FEA_ETIMEOUT, "a bounded wait for a tile's input copy gave up");
     return fail(FEA_EDEGENERATE, "degenerate element (det J == 0 or det F <= 0); NaN written for it");
   }

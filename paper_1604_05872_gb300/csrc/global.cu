@@ -1,0 +1,140 @@
+// Global assembly (the step after local assembly, Section 2: A = sum_K of the
+// element matrices at their global degrees of freedom): the CSR sparsity
+// pattern of a mesh's element-to-DOF map, built on the host, and the GPU
+// scatter-add of element matrices into the CSR values.
+//
+// Scatter: one thread per (element, local row i); the row's CSR segment is the
+// same for every local column j, each column is found by binary search in the
+// sorted segment and added with an FP64 atomic.  A column missing from the
+// pattern, a DOF outside [0, nrows) or a row segment outside [0, nnz) is
+// skipped and flagged (the next fea_sync returns FEA_EINVAL): every access
+// stays inside the arrays' declared sizes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fea.h"
+#include "common.cuh"
+
+namespace fea {
+
+constexpr unsigned ERR_PATTERN = 8u;
+
+template <typename TE>
+__global__ void __launch_bounds__(256) scatter_csr_kernel(int64_t E, int n, const int32_t* __restrict__ dofs,
+                                                          const TE* __restrict__ elem, int64_t nrows,
+                                                          const int64_t* __restrict__ row_ptr,
+                                                          const int32_t* __restrict__ col_idx, int64_t nnz,
+                                                          double* values, unsigned* err) {
+  const int64_t rows = E * n;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < rows; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = w / n;
+    const int i = (int)(w - e * n);
+    const int32_t* de = dofs + e * n;
+    const int32_t r = __ldg(de + i);
+    if (r < 0 || r >= nrows) {
+      flag_error(err, ERR_PATTERN);
+      continue;
+    }
+    const int64_t lo0 = __ldg(row_ptr + r), hi0 = __ldg(row_ptr + r + 1);
+    if (lo0 < 0 || hi0 < lo0 || hi0 > nnz) {
+      flag_error(err, ERR_PATTERN);
+      continue;
+    }
+    const TE* a = elem + (e * n + i) * (int64_t)n;
+    for (int j = 0; j < n; ++j) {
+      const int32_t c = __ldg(de + j);
+      int64_t lo = lo0, hi = hi0;  // first position with col_idx >= c
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(col_idx + mid) < c) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < hi0 && __ldg(col_idx + lo) == c) atomicAdd(values + lo, (double)__ldg(a + j));
+      else flag_error(err, ERR_PATTERN);
+    }
+  }
+}
+
+int set_error(int code, const char* msg);
+int check_device_ptr(const void* p, const char* what, bool allow_null);
+struct DevState;
+int get_dev_state(DevState** out);
+unsigned* device_error_word(DevState* st);
+int device_sms(DevState* st);
+
+int scatter_impl(int64_t E, int n, const int32_t* dofs, const void* elem, int elem_f32, int64_t nrows,
+                 const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz, double* values, void* stream) {
+  if (E < 0 || n < 1 || nrows < 0 || nnz < 0) return set_error(FEA_EINVAL, "negative size or empty local dimension");
+  if (elem_f32 != 0 && elem_f32 != 1) return set_error(FEA_EINVAL, "elem_f32 must be 0 or 1");
+  if (E == 0) return FEA_OK;
+  DevState* st = nullptr;
+  int rc = get_dev_state(&st);
+  if (rc) return rc;
+  if ((rc = check_device_ptr(dofs, "dofs", false))) return rc;
+  if ((rc = check_device_ptr(elem, "elem", false))) return rc;
+  if ((rc = check_device_ptr(row_ptr, "row_ptr", false))) return rc;
+  if ((rc = check_device_ptr(col_idx, "col_idx", nnz == 0))) return rc;
+  if ((rc = check_device_ptr(values, "values", nnz == 0))) return rc;
+  const int64_t rows = E * n;
+  const int64_t grid = std::min<int64_t>((rows + 255) / 256, (int64_t)device_sms(st) * 8);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* err = device_error_word(st);
+  if (elem_f32)
+    scatter_csr_kernel<float><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, static_cast<const float*>(elem), nrows, row_ptr,
+                                                            col_idx, nnz, values, err);
+  else
+    scatter_csr_kernel<double><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, static_cast<const double*>(elem), nrows, row_ptr,
+                                                             col_idx, nnz, values, err);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  return FEA_OK;
+}
+
+// CSR pattern of sum_K (dofs_K x dofs_K): sorted unique columns per row.
+int csr_pattern_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, int64_t* row_ptr, int32_t* col_idx,
+                     int64_t* nnz) {
+  if (E < 0 || n < 1 || nrows < 0 || !nnz || (E > 0 && !dofs)) return set_error(FEA_EINVAL, "bad pattern arguments");
+  std::vector<std::vector<int32_t>> cols((size_t)nrows);
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t* d = dofs + e * n;
+    for (int i = 0; i < n; ++i) {
+      if (d[i] < 0 || d[i] >= nrows) return set_error(FEA_EINVAL, "a DOF index is outside [0, nrows)");
+      for (int j = 0; j < n; ++j) cols[(size_t)d[i]].push_back(d[j]);
+    }
+  }
+  int64_t total = 0;
+  for (auto& c : cols) {
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    total += (int64_t)c.size();
+  }
+  if (col_idx && *nnz < total) return set_error(FEA_EINVAL, "col_idx is smaller than the pattern (query nnz first)");
+  *nnz = total;
+  if (row_ptr) {
+    int64_t k = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+      row_ptr[r] = k;
+      if (col_idx) std::copy(cols[(size_t)r].begin(), cols[(size_t)r].end(), col_idx + k);
+      k += (int64_t)cols[(size_t)r].size();
+    }
+    row_ptr[nrows] = k;
+  }
+  return FEA_OK;
+}
+
+}  // namespace fea
+
+extern "C" int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const void* elem, int elem_f32, int64_t nrows,
+                                   const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz, double* values,
+                                   void* stream) {
+  return fea::scatter_impl(E, n, dofs, elem, elem_f32, nrows, row_ptr, col_idx, nnz, values, stream);
+}
+
+extern "C" int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nrows, int64_t* row_ptr,
+                               int32_t* col_idx, int64_t* nnz) {
+  return fea::csr_pattern_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz);
+}

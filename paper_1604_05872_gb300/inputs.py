@@ -146,3 +146,56 @@ def shard(E, rank, world):
     base, extra = divmod(E, world)
     start = rank * base + min(rank, extra)
     return start, base + (1 if rank < extra else 0)
+
+
+def box_mesh(k, p, jitter=0.0, seed=SEED):
+    """Conforming tetrahedral mesh of the unit cube: k^3 cubes, each cut into the
+    6 tetrahedra of the path subdivision (one per ordering of the axes, all
+    sharing the cube's main diagonal), positively oriented.  Returns
+    (coords [E, 4, 3], dofs [E, n_p] int32 global DOF of each local DOF for
+    p = 1 or 2 in the library's local order -- vertices, then the edges
+    (2,3), (1,3), (1,2), (0,3), (0,2), (0,1) -- and the DOF count).  `jitter`
+    moves interior vertices by U[-jitter, jitter] / k per axis."""
+    import itertools
+    if p not in (1, 2):
+        raise ValueError("box_mesh numbers P1 and P2 DOFs")
+    m = k + 1
+    g = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"), axis=-1).reshape(-1, 3)
+    pts = g.astype(np.float64) / k
+    if jitter:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        inner = np.all((g > 0) & (g < k), axis=1)
+        pts[inner] += rng.uniform(-jitter, jitter, size=(int(inner.sum()), 3)) / k
+    vid = lambda i, j, l: (i * m + j) * m + l
+    tets = []
+    for i in range(k):
+        for j in range(k):
+            for l in range(k):
+                for perm in itertools.permutations(range(3)):
+                    c = np.array([i, j, l])
+                    path = [c.copy()]
+                    for ax in perm:
+                        c = c.copy()
+                        c[ax] += 1
+                        path.append(c)
+                    tets.append([vid(*v) for v in path])
+    tets = np.array(tets, dtype=np.int64)
+    d = pts[tets[:, 1:]] - pts[tets[:, :1]]
+    neg = np.einsum("ei,ei->e", d[:, 0], np.cross(d[:, 1], d[:, 2])) < 0
+    tets[neg, 2], tets[neg, 3] = tets[neg, 3].copy(), tets[neg, 2].copy()
+    coords = np.ascontiguousarray(pts[tets])
+    nv = pts.shape[0]
+    if p == 1:
+        return coords, tets.astype(np.int32), nv
+    pairs = [(2, 3), (1, 3), (1, 2), (0, 3), (0, 2), (0, 1)]
+    ends = np.stack([np.sort(np.stack([tets[:, a], tets[:, b]], axis=1), axis=1) for a, b in pairs], axis=1)
+    key = ends[..., 0] * nv + ends[..., 1]
+    uniq, inv = np.unique(key.reshape(-1), return_inverse=True)
+    dofs = np.concatenate([tets, nv + inv.reshape(-1, 6)], axis=1).astype(np.int32)
+    return coords, dofs, nv + uniq.size
+
+
+def vector_dofs(dofs):
+    """Global DOFs of a vector field: local 3 a + c -> global 3 dof[a] + c."""
+    d = np.asarray(dofs, dtype=np.int64)
+    return (3 * d[:, :, None] + np.arange(3)[None, None, :]).reshape(d.shape[0], -1).astype(np.int32)

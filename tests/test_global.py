@@ -1,0 +1,110 @@
+"""Global assembly: the CSR pattern builder (host, C ABI) against a library
+sparse sum, the reference global matrices against closed forms on the unit
+cube, and the GPU scatter-add against the reference."""
+import numpy as np
+import pytest
+
+from oracle import global_ref
+from paper_1604_05872_gb300 import inputs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_1604_05872_gb300 import build as fbuild
+    import paper_1604_05872_gb300 as fea
+    fbuild.build()
+    return fea.load()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_csr_pattern_matches_library_sparse_sum(p):
+    import paper_1604_05872_gb300 as fea
+    coords, dofs, nd = inputs.box_mesh(3, p, jitter=0.2)
+    for d, nrows in ((dofs, nd), (inputs.vector_dofs(dofs), 3 * nd)):
+        row_ptr, col_idx = fea.csr_pattern(d, nrows)
+        n = d.shape[1]
+        indptr, indices, _ = global_ref.assemble_csr(d, np.ones((d.shape[0], n, n)), nrows)
+        assert np.array_equal(row_ptr, indptr) and np.array_equal(col_idx, indices)
+    with pytest.raises(fea.FeaError):
+        fea.csr_pattern(dofs, nd - 1)  # a DOF outside [0, nrows)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_reference_global_matrices_on_the_unit_cube(orc, p):
+    """Mass: the entries sum to the volume (1).  Laplacian (Helmholtz with
+    f = 0): zero row sums, and u^T K u = int |grad u|^2 = 1 for u = x, exact
+    for P1 and P2; both symmetric."""
+    coords, dofs, nd = inputs.box_mesh(3, p, jitter=0.2)
+    E, n = dofs.shape
+    M = orc.assemble(orc.MASS, p, coords)
+    K = orc.assemble(orc.HELMHOLTZ, p, coords, np.zeros((E, n)))
+    _, _, mdata = global_ref.assemble_csr(dofs, M, nd)
+    assert abs(mdata.sum() - 1.0) < 1e-13
+    import scipy.sparse as sp
+    indptr, indices, kdata = global_ref.assemble_csr(dofs, K, nd)
+    Kg = sp.csr_matrix((kdata, indices, indptr), shape=(nd, nd))
+    assert np.abs(Kg @ np.ones(nd)).max() < 1e-12
+    assert abs(Kg - Kg.T).max() < 1e-13
+    # nodal values of u = x at every global DOF (vertices, and edge midpoints for P2)
+    x = np.zeros(nd)
+    nodes = {1: [0, 1, 2, 3], 2: list(range(10))}[p]
+    pos = np.concatenate([coords, 0.5 * (coords[:, [2, 1, 1, 0, 0, 0]] + coords[:, [3, 3, 2, 3, 2, 1]])], axis=1)
+    x[dofs.reshape(-1)] = pos[:, nodes, 0].reshape(-1)
+    assert abs(x @ (Kg @ x) - 1.0) < 1e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form,p", [(0, 1), (1, 2), (2, 1), (2, 2), (3, 2)])
+def test_gpu_global_assembly_matches_reference(fea, orc, form, p):
+    import torch
+    coords, dofs, nd = inputs.box_mesh(8, p, jitter=0.1)  # 3072 elements
+    E = coords.shape[0]
+    rng = np.random.default_rng(7)
+    scale = np.full(E, 1.0 / 8)  # element size: displacement gradients as on the unit-size workloads
+    coeffs = inputs.random_coeffs(form, p, E, rng, scale)
+    d = dofs if form < 2 else inputs.vector_dofs(dofs)
+    nrows = nd if form < 2 else 3 * nd
+    row_ptr, col_idx = fea.csr_pattern(d, nrows)
+    c = torch.from_numpy(coords).cuda()
+    f = None if form == 0 else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
+    elem = fea.assemble(form, p, c, f)
+    dd = torch.from_numpy(d).cuda()
+    rp = torch.from_numpy(row_ptr).cuda()
+    ci = torch.from_numpy(col_idx).cuda()
+    vals = torch.zeros(col_idx.shape[0], dtype=torch.float64, device="cuda")
+    fea.scatter_add_csr(dd, elem, rp, ci, vals)
+    fea.sync()
+    got = vals.cpu().numpy()
+    # the same element matrices summed by the library sparse sum: summation order only
+    _, _, same = global_ref.assemble_csr(d, elem.cpu().numpy(), nrows)
+    assert np.abs(got - same).max() <= 1e-12 * np.abs(same).max()
+    # against the oracle's element matrices: the FP32 contraction's tolerance
+    ref_elem = orc.assemble(form, p, coords, coeffs)
+    _, _, ref = global_ref.assemble_csr(d, ref_elem, nrows)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    # FP32 element input gives the same sums of the rounded values
+    vals32 = torch.zeros_like(vals)
+    fea.scatter_add_csr(dd, fea.assemble(form, p, c, f, out_f32=True), rp, ci, vals32)
+    fea.sync()
+    assert torch.allclose(vals32, vals, rtol=0, atol=1e-12 * float(vals.abs().max()))
+
+
+@pytest.mark.gpu
+def test_gpu_scatter_outside_pattern_is_flagged(fea):
+    import torch
+    coords, dofs, nd = inputs.box_mesh(2, 1)
+    row_ptr, col_idx = fea.csr_pattern(np.arange(nd, dtype=np.int32).reshape(-1, 1), nd)  # diagonal only
+    c = torch.from_numpy(coords).cuda()
+    elem = fea.assemble(0, 1, c)
+    vals = torch.zeros(col_idx.shape[0], dtype=torch.float64, device="cuda")
+    fea.scatter_add_csr(torch.from_numpy(dofs).cuda(), elem, torch.from_numpy(row_ptr).cuda(),
+                        torch.from_numpy(col_idx).cuda(), vals)
+    with pytest.raises(fea.FeaError) as ei:
+        fea.sync()
+    assert ei.value.code == fea.EINVAL
+    bad = dofs.copy()
+    bad[3, 2] = nd + 5  # a DOF outside the rows: skipped on the device, flagged
+    fea.scatter_add_csr(torch.from_numpy(bad).cuda(), elem, torch.from_numpy(row_ptr).cuda(),
+                        torch.from_numpy(col_idx).cuda(), vals)
+    with pytest.raises(fea.FeaError):
+        fea.sync()
