@@ -178,6 +178,17 @@ int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const void* elem,
                         int64_t nrows, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz,
                         double* values, void* stream);
 
+/* The same scatter split in two for repeated assembly on one mesh:
+ * fea_csr_scatter_map writes once, for every (e, i, j), the CSR position of
+ * column dofs[e][j] in row dofs[e][i] into map [E][n][n] (int64, device; -1
+ * and FEA_EINVAL at the next fea_sync where the pattern has no entry);
+ * fea_scatter_add_csr_mapped then does values[map[e][i][j]] += elem[e][i][j]
+ * with coalesced reads and no search. */
+int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
+                        const int32_t* col_idx, int64_t nnz, int64_t* map, void* stream);
+int fea_scatter_add_csr_mapped(int64_t E, int n, const int64_t* map, const void* elem, int elem_f32,
+                               int64_t nnz, double* values, void* stream);
+
 /* Uneven batch of requests (forms, degrees and sizes mixed) in one CUDA graph
  * launch, captured once per distinct batch and replayed: each request runs the
  * persistent kernel it would run alone (its own tile, registers and shared

@@ -24,6 +24,7 @@ VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
            "fea_assemble_vector", "fea_csr_pattern", "fea_scatter_add_csr",
+           "fea_csr_scatter_map", "fea_scatter_add_csr_mapped",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_fused",
            "fea_assemble_batch_noalloc",
            "fea_sync", "fea_plan", "fea_plan_flop",
@@ -84,6 +85,8 @@ def load(path=None):
     lib.fea_assemble_vector.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_csr_pattern.argtypes = [i64, i, vp, i64, vp, vp, P(i64)]
     lib.fea_scatter_add_csr.argtypes = [i64, i, vp, vp, i, i64, vp, vp, i64, vp, vp]
+    lib.fea_csr_scatter_map.argtypes = [i64, i, vp, i64, vp, vp, i64, vp, vp]
+    lib.fea_scatter_add_csr_mapped.argtypes = [i64, i, vp, vp, i, i64, vp, vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
@@ -227,6 +230,25 @@ def scatter_add_csr(dofs, elem, row_ptr, col_idx, values, stream=None):
     f32 = elem.dtype == torch.float32
     _check(load().fea_scatter_add_csr(E, n, _ptr(dofs), _ptr(elem), int(f32), row_ptr.shape[0] - 1, _ptr(row_ptr),
                                       _ptr(col_idx), col_idx.shape[0], _ptr(values), _stream_ptr(stream)))
+    return values
+
+
+def csr_scatter_map(dofs, row_ptr, col_idx, stream=None):
+    """CSR position of every (element, i, j) [E, n, n] int64 (device); fea_csr_scatter_map."""
+    import torch
+    E, n = dofs.shape
+    m = torch.empty((E, n, n), dtype=torch.int64, device=dofs.device)
+    _check(load().fea_csr_scatter_map(E, n, _ptr(dofs), row_ptr.shape[0] - 1, _ptr(row_ptr), _ptr(col_idx),
+                                      col_idx.shape[0], _ptr(m), _stream_ptr(stream)))
+    return m
+
+
+def scatter_add_csr_mapped(scatter_map, elem, values, stream=None):
+    """values[map] += elem (device); fea_scatter_add_csr_mapped.  Returns `values`."""
+    import torch
+    E, n, _ = scatter_map.shape
+    _check(load().fea_scatter_add_csr_mapped(E, n, _ptr(scatter_map), _ptr(elem), int(elem.dtype == torch.float32),
+                                             values.shape[0], _ptr(values), _stream_ptr(stream)))
     return values
 
 

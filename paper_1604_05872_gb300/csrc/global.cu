@@ -59,6 +59,56 @@ __global__ void __launch_bounds__(256) scatter_csr_kernel(int64_t E, int n, cons
   }
 }
 
+// The CSR position of every (element, i, j): the same search as the scatter,
+// done once; -1 (and the error flag) where the pattern has no such entry.
+__global__ void __launch_bounds__(256) scatter_map_kernel(int64_t E, int n, const int32_t* __restrict__ dofs,
+                                                          int64_t nrows, const int64_t* __restrict__ row_ptr,
+                                                          const int32_t* __restrict__ col_idx, int64_t nnz,
+                                                          int64_t* map, unsigned* err) {
+  const int64_t rows = E * n;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < rows; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = w / n;
+    const int32_t* de = dofs + e * n;
+    const int32_t r = __ldg(de + (w - e * n));
+    int64_t* m = map + w * n;
+    int64_t lo0 = 0, hi0 = 0;
+    const bool row_ok = r >= 0 && r < nrows;
+    if (row_ok) {
+      lo0 = __ldg(row_ptr + r);
+      hi0 = __ldg(row_ptr + r + 1);
+    }
+    const bool seg_ok = row_ok && lo0 >= 0 && hi0 >= lo0 && hi0 <= nnz;
+    for (int j = 0; j < n; ++j) {
+      int64_t pos = -1;
+      if (seg_ok) {
+        const int32_t c = __ldg(de + j);
+        int64_t lo = lo0, hi = hi0;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (__ldg(col_idx + mid) < c) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < hi0 && __ldg(col_idx + lo) == c) pos = lo;
+      }
+      if (pos < 0) flag_error(err, ERR_PATTERN);
+      m[j] = pos;
+    }
+  }
+}
+
+// values[map[k]] += elem[k] over all E n^2 entries: coalesced reads of the map
+// and the element matrices, one FP64 atomic per entry.
+template <typename TE>
+__global__ void __launch_bounds__(256) scatter_mapped_kernel(int64_t total, const int64_t* __restrict__ map,
+                                                             const TE* __restrict__ elem, int64_t nnz, double* values,
+                                                             unsigned* err) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pos = __ldg(map + k);
+    if (pos >= 0 && pos < nnz) atomicAdd(values + pos, (double)__ldg(elem + k));
+    else flag_error(err, ERR_PATTERN);
+  }
+}
+
 int set_error(int code, const char* msg);
 int check_device_ptr(const void* p, const char* what, bool allow_null);
 struct DevState;
@@ -89,6 +139,51 @@ int scatter_impl(int64_t E, int n, const int32_t* dofs, const void* elem, int el
   else
     scatter_csr_kernel<double><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, static_cast<const double*>(elem), nrows, row_ptr,
                                                              col_idx, nnz, values, err);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  return FEA_OK;
+}
+
+int scatter_map_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
+                     const int32_t* col_idx, int64_t nnz, int64_t* map, void* stream) {
+  if (E < 0 || n < 1 || nrows < 0 || nnz < 0) return set_error(FEA_EINVAL, "negative size or empty local dimension");
+  if (E == 0) return FEA_OK;
+  DevState* st = nullptr;
+  int rc = get_dev_state(&st);
+  if (rc) return rc;
+  if ((rc = check_device_ptr(dofs, "dofs", false))) return rc;
+  if ((rc = check_device_ptr(row_ptr, "row_ptr", false))) return rc;
+  if ((rc = check_device_ptr(col_idx, "col_idx", nnz == 0))) return rc;
+  if ((rc = check_device_ptr(map, "map", false))) return rc;
+  const int64_t rows = E * n;
+  const int64_t grid = std::min<int64_t>((rows + 255) / 256, (int64_t)device_sms(st) * 8);
+  scatter_map_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz, map,
+                                                                        device_error_word(st));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  return FEA_OK;
+}
+
+int scatter_mapped_impl(int64_t E, int n, const int64_t* map, const void* elem, int elem_f32, int64_t nnz,
+                        double* values, void* stream) {
+  if (E < 0 || n < 1 || nnz < 0) return set_error(FEA_EINVAL, "negative size or empty local dimension");
+  if (elem_f32 != 0 && elem_f32 != 1) return set_error(FEA_EINVAL, "elem_f32 must be 0 or 1");
+  if (E == 0) return FEA_OK;
+  DevState* st = nullptr;
+  int rc = get_dev_state(&st);
+  if (rc) return rc;
+  if ((rc = check_device_ptr(map, "map", false))) return rc;
+  if ((rc = check_device_ptr(elem, "elem", false))) return rc;
+  if ((rc = check_device_ptr(values, "values", nnz == 0))) return rc;
+  const int64_t total = E * n * n;
+  const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)device_sms(st) * 8);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* err = device_error_word(st);
+  if (elem_f32)
+    scatter_mapped_kernel<float><<<(unsigned)grid, 256, 0, s>>>(total, map, static_cast<const float*>(elem), nnz, values, err);
+  else
+    scatter_mapped_kernel<double><<<(unsigned)grid, 256, 0, s>>>(total, map, static_cast<const double*>(elem), nnz, values,
+                                                                 err);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
   return FEA_OK;
@@ -137,4 +232,14 @@ extern "C" int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const 
 extern "C" int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nrows, int64_t* row_ptr,
                                int32_t* col_idx, int64_t* nnz) {
   return fea::csr_pattern_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz);
+}
+
+extern "C" int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
+                                   const int32_t* col_idx, int64_t nnz, int64_t* map, void* stream) {
+  return fea::scatter_map_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz, map, stream);
+}
+
+extern "C" int fea_scatter_add_csr_mapped(int64_t E, int n, const int64_t* map, const void* elem, int elem_f32,
+                                          int64_t nnz, double* values, void* stream) {
+  return fea::scatter_mapped_impl(E, n, map, elem, elem_f32, nnz, values, stream);
 }

@@ -166,20 +166,15 @@ def box_mesh(k, p, jitter=0.0, seed=SEED):
         rng = np.random.Generator(np.random.PCG64(seed))
         inner = np.all((g > 0) & (g < k), axis=1)
         pts[inner] += rng.uniform(-jitter, jitter, size=(int(inner.sum()), 3)) / k
-    vid = lambda i, j, l: (i * m + j) * m + l
-    tets = []
-    for i in range(k):
-        for j in range(k):
-            for l in range(k):
-                for perm in itertools.permutations(range(3)):
-                    c = np.array([i, j, l])
-                    path = [c.copy()]
-                    for ax in perm:
-                        c = c.copy()
-                        c[ax] += 1
-                        path.append(c)
-                    tets.append([vid(*v) for v in path])
-    tets = np.array(tets, dtype=np.int64)
+    cube = np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"), axis=-1).reshape(-1, 1, 3)
+    paths = []
+    for perm in itertools.permutations(range(3)):  # one tetrahedron per ordering of the axes
+        steps = np.zeros((4, 3), dtype=np.int64)
+        for t, ax in enumerate(perm):
+            steps[t + 1:, ax] += 1
+        paths.append(steps)
+    corner = cube + np.stack(paths)[None, :, :, :].reshape(1, 6 * 4, 3)  # [cubes, 6 * 4, 3]
+    tets = ((corner[..., 0] * m + corner[..., 1]) * m + corner[..., 2]).reshape(-1, 4).astype(np.int64)
     d = pts[tets[:, 1:]] - pts[tets[:, :1]]
     neg = np.einsum("ei,ei->e", d[:, 0], np.cross(d[:, 1], d[:, 2])) < 0
     tets[neg, 2], tets[neg, 3] = tets[neg, 3].copy(), tets[neg, 2].copy()

@@ -82,6 +82,11 @@ def test_gpu_global_assembly_matches_reference(fea, orc, form, p):
     ref_elem = orc.assemble(form, p, coords, coeffs)
     _, _, ref = global_ref.assemble_csr(d, ref_elem, nrows)
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    # the two-step form (positions once, then search-free scatter) gives the same sums
+    smap = fea.csr_scatter_map(dd, rp, ci)
+    vals_m = fea.scatter_add_csr_mapped(smap, elem, torch.zeros_like(vals))
+    fea.sync()
+    assert torch.allclose(vals_m, vals, rtol=0, atol=1e-12 * float(vals.abs().max()))
     # FP32 element input gives the same sums of the rounded values
     vals32 = torch.zeros_like(vals)
     fea.scatter_add_csr(dd, fea.assemble(form, p, c, f, out_f32=True), rp, ci, vals32)
