@@ -44,30 +44,42 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ["common.cuh", "layout.h", "pre_stream.cuh", "planner.cpp"]  # the timed kernel and its tile rule
+# committed ncu summaries of the timed kernels: profile file and the sources its kernel is built from
+PROFILES = {
+    "helmholtz_p2_1M": ("helmholtz_p2_pre_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh", "planner.cpp"]),
+    "elasticity_p3_200k": ("elasticity_p3_pre_stream_200k.md",
+                           ["common.cuh", "layout.h", "pre_stream.cuh", "stream_batched.cuh", "pre_vec_stream.cuh",
+                            "pre_vec.cuh", "sym.cuh", "planner.cpp"]),
+    "neohookean_p2_500k": ("neohookean_p2_se_500k.md",
+                           ["common.cuh", "layout.h", "launch.cuh", "se_vec.cuh", "sym.cuh", "log_f64.cuh",
+                            "log_table.h", "planner.cpp"]),
+    "helmholtz_p2_global_1M": ("global_helmholtz_p2_1M.md", ["common.cuh", "global.cu"]),
+}
 
 
-def kernel_source_hash():
+def kernel_source_hash(names):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1604_05872_gb300", "csrc")
-    for name in KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel sources changed since."""
-    path = os.path.join(ROOT, "profiles", "helmholtz_p2_pre_1M.md")
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the workload's timed kernel from its committed ncu
+    summary, or None when there is none or the kernel sources changed since."""
+    if workload not in PROFILES:
+        return None
+    name, sources = PROFILES[workload]
     try:
-        txt = open(path).read()
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
     except OSError:
         return None
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     s = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not s or s.group(1) != kernel_source_hash():
+    if not m or not s or s.group(1) != kernel_source_hash(sources):
         return None
     return float(m.group(1))
 
@@ -225,9 +237,14 @@ FP64_PEAK_TINSTR = 152 * 2 * 2.07e9 / 1e12          # SMs x FP64 lanes per clock
 def fp64_ops_per_element(form, p, variant, Q):
     """FP64 lane-instructions per element of the flop-reduced kernels: 30 for
     the geometry (9 subtractions for J, 18 for the adjugate's 2x2 minors, 3 for
-    det J), plus, per Neo-Hookean point, 21 for the cofactors of F and det F
-    and about 20 for ln det F."""
-    return 30 + (41 * Q if form == 3 else 0)
+    det J), plus NEO_POINT_FP64 per Neo-Hookean point."""
+    return 30 + (NEO_POINT_FP64 * Q if form == 3 else 0)
+
+
+# FP64 lane-instructions per Neo-Hookean point: F = I + grad u (3 additions), the
+# cofactors of F (18) and det F (3), two tests of det F, and ln det F by the
+# table-driven logarithm (13)
+NEO_POINT_FP64 = 3 + 18 + 3 + 2 + 13
 
 
 def main():
@@ -364,7 +381,7 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         roof = {"bound": "alu", "achieved": f64 / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TINSTR,
                 "unit": "T FP64 lane-instructions/s", "peak_kind": "derived: FP64 lanes x clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = profiled_traffic() if args.workload == "helmholtz_p2_1M" and E == E0 and not f32 else None
+    roof["traffic"] = profiled_traffic(args.workload) if E == E0 and not f32 else None
     roof["alg_bytes_per_launch"] = alg_bytes
     roof["bound_times_ms"] = {"hbm": t_hbm * 1e3, "fp32": t_f32 * 1e3, "fp64": t_f64 * 1e3}
     cfg = {"workload": args.workload, "form": ["mass", "helmholtz", "elasticity", "neohookean"][form],
@@ -431,7 +448,7 @@ def run_vector(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     if form == 1:
         flops, f64 = 2 * ns * ns + ns, 20
     else:
-        flops, f64 = Q * (2 * 9 * ns + 2 * 27 + 2 * 27 + 2 * 27 + 18 * ns), 50 + 41 * Q
+        flops, f64 = Q * (2 * 9 * ns + 2 * 27 + 2 * 27 + 2 * 27 + 18 * ns), 50 + NEO_POINT_FP64 * Q
     hbm, peak_kind = peaks()
     alg_bytes, fl, f64t = E * bytes_elem, E * flops, E * f64
     t_hbm, t_f32, t_f64 = alg_bytes / (hbm * 1e9), fl / (FP32_PEAK_TFLOPS * 1e12), f64t / (FP64_PEAK_TINSTR * 1e12)
@@ -524,20 +541,28 @@ def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     fea.sync()
     ms_max = max_over_ranks(ms)
     nnz = col_idx.shape[0]
-    # algorithmic bytes: local assembly (976 B/element), the scatter's reads of the element
-    # matrices and of the position map (800 + 800 B/element), and the CSR values zeroed and
-    # accumulated (3 x 8 B per entry)
-    alg_bytes = E * (976 + 800 + 800) + nnz * 24
+    # algorithmic bytes of the step: local assembly (976 B/element), the scatter's reads of the
+    # element matrices and of the position map (800 B + 100 map entries per element), and the CSR
+    # values zeroed and accumulated (3 x 8 B per entry).  The dominant kernel is the mapped
+    # scatter: its own bytes are the element matrices, the map and one read and one write of
+    # every CSR value.
+    map_bytes = 100 * smap.element_size()
+    alg_bytes = E * (976 + 800 + map_bytes) + nnz * 24
+    scatter_bytes = E * (800 + map_bytes) + nnz * 16
     hbm, peak_kind = peaks()
-    roof = {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-            "peak_kind": peak_kind, "traffic": None, "alg_bytes_per_launch": alg_bytes}
+    roof = {"bound": "hbm", "kernel": "scatter_mapped_kernel<double>",
+            "achieved": scatter_bytes / (ms_scatter * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "peak_kind": peak_kind, "traffic": profiled_traffic(args.workload),
+            "alg_bytes_per_launch": scatter_bytes,
+            "step_achieved": alg_bytes / (ms * 1e-3) / 1e9, "step_alg_bytes": alg_bytes}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["step_frac"] = roof["step_achieved"] / roof["peak"]
     line = {
         "metric": METRIC, "value": E * world / (ms_max * 1e-3), "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "form": "helmholtz", "degree": 2, "elements": E, "dofs": nd,
-                   "nnz": nnz, "local_matrix": "10x10 f64", "global": "CSR f64, FP64 atomics at precomputed positions",
+                   "nnz": nnz, "local_matrix": "10x10 f64", "global": "CSR f64, FP64 atomics at precomputed positions (%s map)" % str(smap.dtype).replace("torch.", ""),
                    "scatter_ms": ms_scatter, "scatter_with_search_ms": ms_search, "pattern_host_s": t_pattern,
                    "l2": "%.0f MB per step > 129 MB L2; no flush" % (alg_bytes / 1e6)},
         "roofline": roof, "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "e2e": None,

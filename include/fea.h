@@ -154,6 +154,13 @@ int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host
 int fea_assemble_vector(int form, int degree, int64_t E, const double* coords,
                         const double* coeffs, void* out, const fea_options* opt, void* stream);
 
+/* The natural logarithm the Neo-Hookean kernels evaluate ln det F with (FP64
+ * arithmetic, table-driven: Tang, ACM TOMS 16(4), 1990; 13 FP64 operations),
+ * applied to n doubles: y[i] = ln x[i] (DEVICE arrays, on `stream`).  A few
+ * units in the last place for finite x > 0; unspecified for other x.  Exposed
+ * so that its accuracy can be checked against other implementations. */
+int fea_log_f64(const double* x, double* y, int64_t n, void* stream);
+
 /* Global assembly (the sum over elements of the element matrices at their
  * global degrees of freedom).
  *
@@ -180,13 +187,15 @@ int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const void* elem,
 
 /* The same scatter split in two for repeated assembly on one mesh:
  * fea_csr_scatter_map writes once, for every (e, i, j), the CSR position of
- * column dofs[e][j] in row dofs[e][i] into map [E][n][n] (int64, device; -1
- * and FEA_EINVAL at the next fea_sync where the pattern has no entry);
+ * column dofs[e][j] in row dofs[e][i] into map [E][n][n] (device; int32 when
+ * map_i64 = 0, which needs nnz < 2^31, else FEA_EINVAL; int64 when map_i64 = 1;
+ * -1 and FEA_EINVAL at the next fea_sync where the pattern has no entry);
  * fea_scatter_add_csr_mapped then does values[map[e][i][j]] += elem[e][i][j]
- * with coalesced reads and no search. */
+ * with coalesced reads and no search (map_i64 as the map was written; a
+ * position outside [0, nnz) is skipped and flagged like a missing entry). */
 int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
-                        const int32_t* col_idx, int64_t nnz, int64_t* map, void* stream);
-int fea_scatter_add_csr_mapped(int64_t E, int n, const int64_t* map, const void* elem, int elem_f32,
+                        const int32_t* col_idx, int64_t nnz, void* map, int map_i64, void* stream);
+int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, const void* elem, int elem_f32,
                                int64_t nnz, double* values, void* stream);
 
 /* Uneven batch of requests (forms, degrees and sizes mixed) in one CUDA graph

@@ -24,7 +24,7 @@ VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
            "fea_assemble_vector", "fea_csr_pattern", "fea_scatter_add_csr",
-           "fea_csr_scatter_map", "fea_scatter_add_csr_mapped",
+           "fea_csr_scatter_map", "fea_scatter_add_csr_mapped", "fea_log_f64",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_fused",
            "fea_assemble_batch_noalloc",
            "fea_sync", "fea_plan", "fea_plan_flop",
@@ -85,8 +85,9 @@ def load(path=None):
     lib.fea_assemble_vector.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_csr_pattern.argtypes = [i64, i, vp, i64, vp, vp, P(i64)]
     lib.fea_scatter_add_csr.argtypes = [i64, i, vp, vp, i, i64, vp, vp, i64, vp, vp]
-    lib.fea_csr_scatter_map.argtypes = [i64, i, vp, i64, vp, vp, i64, vp, vp]
-    lib.fea_scatter_add_csr_mapped.argtypes = [i64, i, vp, vp, i, i64, vp, vp]
+    lib.fea_csr_scatter_map.argtypes = [i64, i, vp, i64, vp, vp, i64, vp, i, vp]
+    lib.fea_log_f64.argtypes = [vp, vp, i64, vp]
+    lib.fea_scatter_add_csr_mapped.argtypes = [i64, i, vp, i, vp, i, i64, vp, vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
@@ -233,21 +234,39 @@ def scatter_add_csr(dofs, elem, row_ptr, col_idx, values, stream=None):
     return values
 
 
-def csr_scatter_map(dofs, row_ptr, col_idx, stream=None):
-    """CSR position of every (element, i, j) [E, n, n] int64 (device); fea_csr_scatter_map."""
+def csr_scatter_map(dofs, row_ptr, col_idx, stream=None, index_dtype=None):
+    """CSR position of every (element, i, j) [E, n, n] (device); fea_csr_scatter_map.  int32
+    when the pattern has fewer than 2^31 entries (index_dtype=None), else int64."""
     import torch
     E, n = dofs.shape
-    m = torch.empty((E, n, n), dtype=torch.int64, device=dofs.device)
+    nnz = col_idx.shape[0]
+    if index_dtype is None:
+        index_dtype = torch.int32 if nnz < 2 ** 31 else torch.int64
+    m = torch.empty((E, n, n), dtype=index_dtype, device=dofs.device)
     _check(load().fea_csr_scatter_map(E, n, _ptr(dofs), row_ptr.shape[0] - 1, _ptr(row_ptr), _ptr(col_idx),
-                                      col_idx.shape[0], _ptr(m), _stream_ptr(stream)))
+                                      nnz, _ptr(m), int(index_dtype == torch.int64), _stream_ptr(stream)))
     return m
+
+
+def log_f64(x, stream=None):
+    """ln x of a float64 device tensor by the kernels' table-driven FP64 logarithm; fea_log_f64."""
+    import torch
+    x = x.contiguous()
+    if x.dtype != torch.float64:
+        raise TypeError("log_f64 takes float64")
+    y = torch.empty_like(x)
+    _check(load().fea_log_f64(_ptr(x), _ptr(y), x.numel(), _stream_ptr(stream)))
+    return y
 
 
 def scatter_add_csr_mapped(scatter_map, elem, values, stream=None):
     """values[map] += elem (device); fea_scatter_add_csr_mapped.  Returns `values`."""
     import torch
     E, n, _ = scatter_map.shape
-    _check(load().fea_scatter_add_csr_mapped(E, n, _ptr(scatter_map), _ptr(elem), int(elem.dtype == torch.float32),
+    if scatter_map.dtype not in (torch.int32, torch.int64):
+        raise TypeError("scatter map must be int32 or int64")
+    _check(load().fea_scatter_add_csr_mapped(E, n, _ptr(scatter_map), int(scatter_map.dtype == torch.int64),
+                                             _ptr(elem), int(elem.dtype == torch.float32),
                                              values.shape[0], _ptr(values), _stream_ptr(stream)))
     return values
 

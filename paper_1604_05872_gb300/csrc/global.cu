@@ -61,16 +61,18 @@ __global__ void __launch_bounds__(256) scatter_csr_kernel(int64_t E, int n, cons
 
 // The CSR position of every (element, i, j): the same search as the scatter,
 // done once; -1 (and the error flag) where the pattern has no such entry.
+// TM is int32_t (patterns with nnz < 2^31) or int64_t.
+template <typename TM>
 __global__ void __launch_bounds__(256) scatter_map_kernel(int64_t E, int n, const int32_t* __restrict__ dofs,
                                                           int64_t nrows, const int64_t* __restrict__ row_ptr,
                                                           const int32_t* __restrict__ col_idx, int64_t nnz,
-                                                          int64_t* map, unsigned* err) {
+                                                          TM* map, unsigned* err) {
   const int64_t rows = E * n;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < rows; w += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = w / n;
     const int32_t* de = dofs + e * n;
     const int32_t r = __ldg(de + (w - e * n));
-    int64_t* m = map + w * n;
+    TM* m = map + w * n;
     int64_t lo0 = 0, hi0 = 0;
     const bool row_ok = r >= 0 && r < nrows;
     if (row_ok) {
@@ -91,15 +93,15 @@ __global__ void __launch_bounds__(256) scatter_map_kernel(int64_t E, int n, cons
         if (lo < hi0 && __ldg(col_idx + lo) == c) pos = lo;
       }
       if (pos < 0) flag_error(err, ERR_PATTERN);
-      m[j] = pos;
+      m[j] = (TM)pos;
     }
   }
 }
 
 // values[map[k]] += elem[k] over all E n^2 entries: coalesced reads of the map
 // and the element matrices, one FP64 atomic per entry.
-template <typename TE>
-__global__ void __launch_bounds__(256) scatter_mapped_kernel(int64_t total, const int64_t* __restrict__ map,
+template <typename TE, typename TM>
+__global__ void __launch_bounds__(256) scatter_mapped_kernel(int64_t total, const TM* __restrict__ map,
                                                              const TE* __restrict__ elem, int64_t nnz, double* values,
                                                              unsigned* err) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
@@ -144,9 +146,13 @@ int scatter_impl(int64_t E, int n, const int32_t* dofs, const void* elem, int el
   return FEA_OK;
 }
 
+constexpr int64_t kMaxMap32 = 2147483647;  // largest position an int32 map holds
+
 int scatter_map_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
-                     const int32_t* col_idx, int64_t nnz, int64_t* map, void* stream) {
+                     const int32_t* col_idx, int64_t nnz, void* map, int map_i64, void* stream) {
   if (E < 0 || n < 1 || nrows < 0 || nnz < 0) return set_error(FEA_EINVAL, "negative size or empty local dimension");
+  if (map_i64 != 0 && map_i64 != 1) return set_error(FEA_EINVAL, "map_i64 must be 0 or 1");
+  if (!map_i64 && nnz > kMaxMap32) return set_error(FEA_EINVAL, "nnz >= 2^31 needs an int64 map");
   if (E == 0) return FEA_OK;
   DevState* st = nullptr;
   int rc = get_dev_state(&st);
@@ -157,17 +163,33 @@ int scatter_map_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, const
   if ((rc = check_device_ptr(map, "map", false))) return rc;
   const int64_t rows = E * n;
   const int64_t grid = std::min<int64_t>((rows + 255) / 256, (int64_t)device_sms(st) * 8);
-  scatter_map_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz, map,
-                                                                        device_error_word(st));
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* err = device_error_word(st);
+  if (map_i64)
+    scatter_map_kernel<int64_t><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz,
+                                                               static_cast<int64_t*>(map), err);
+  else
+    scatter_map_kernel<int32_t><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz,
+                                                               static_cast<int32_t*>(map), err);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
   return FEA_OK;
 }
 
-int scatter_mapped_impl(int64_t E, int n, const int64_t* map, const void* elem, int elem_f32, int64_t nnz,
+template <typename TM>
+void launch_mapped(unsigned grid, cudaStream_t s, int64_t total, const TM* map, const void* elem, int elem_f32,
+                   int64_t nnz, double* values, unsigned* err) {
+  if (elem_f32)
+    scatter_mapped_kernel<float, TM><<<grid, 256, 0, s>>>(total, map, static_cast<const float*>(elem), nnz, values, err);
+  else
+    scatter_mapped_kernel<double, TM><<<grid, 256, 0, s>>>(total, map, static_cast<const double*>(elem), nnz, values, err);
+}
+
+int scatter_mapped_impl(int64_t E, int n, const void* map, int map_i64, const void* elem, int elem_f32, int64_t nnz,
                         double* values, void* stream) {
   if (E < 0 || n < 1 || nnz < 0) return set_error(FEA_EINVAL, "negative size or empty local dimension");
   if (elem_f32 != 0 && elem_f32 != 1) return set_error(FEA_EINVAL, "elem_f32 must be 0 or 1");
+  if (map_i64 != 0 && map_i64 != 1) return set_error(FEA_EINVAL, "map_i64 must be 0 or 1");
   if (E == 0) return FEA_OK;
   DevState* st = nullptr;
   int rc = get_dev_state(&st);
@@ -179,11 +201,10 @@ int scatter_mapped_impl(int64_t E, int n, const int64_t* map, const void* elem, 
   const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)device_sms(st) * 8);
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* err = device_error_word(st);
-  if (elem_f32)
-    scatter_mapped_kernel<float><<<(unsigned)grid, 256, 0, s>>>(total, map, static_cast<const float*>(elem), nnz, values, err);
+  if (map_i64)
+    launch_mapped<int64_t>((unsigned)grid, s, total, static_cast<const int64_t*>(map), elem, elem_f32, nnz, values, err);
   else
-    scatter_mapped_kernel<double><<<(unsigned)grid, 256, 0, s>>>(total, map, static_cast<const double*>(elem), nnz, values,
-                                                                 err);
+    launch_mapped<int32_t>((unsigned)grid, s, total, static_cast<const int32_t*>(map), elem, elem_f32, nnz, values, err);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
   return FEA_OK;
@@ -235,11 +256,11 @@ extern "C" int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nr
 }
 
 extern "C" int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
-                                   const int32_t* col_idx, int64_t nnz, int64_t* map, void* stream) {
-  return fea::scatter_map_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz, map, stream);
+                                   const int32_t* col_idx, int64_t nnz, void* map, int map_i64, void* stream) {
+  return fea::scatter_map_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz, map, map_i64, stream);
 }
 
-extern "C" int fea_scatter_add_csr_mapped(int64_t E, int n, const int64_t* map, const void* elem, int elem_f32,
-                                          int64_t nnz, double* values, void* stream) {
-  return fea::scatter_mapped_impl(E, n, map, elem, elem_f32, nnz, values, stream);
+extern "C" int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, const void* elem,
+                                          int elem_f32, int64_t nnz, double* values, void* stream) {
+  return fea::scatter_mapped_impl(E, n, map, map_i64, elem, elem_f32, nnz, values, stream);
 }

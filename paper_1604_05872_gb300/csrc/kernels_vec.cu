@@ -1,4 +1,7 @@
 // Instantiations of the element-vector kernels (linear forms; P1-P4; FP32 and FP64).
+#include <algorithm>
+
+#include "../../include/fea.h"
 #include "launch.cuh"
 #include "vec_forms.cuh"
 
@@ -18,3 +21,31 @@ const KernelInfo* find_vec_kernel(int form, int p, int prec) {
 }
 
 }  // namespace fea
+
+// ----------------------------------------------------------------------------
+// The kernels' FP64 logarithm (log_f64.cuh) over an array, for its accuracy
+// tests against the hardware library and the host.
+namespace fea {
+
+__global__ void __launch_bounds__(256) log_f64_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = log_f64(__ldg(x + i));
+}
+
+int set_error(int code, const char* msg);
+int check_device_ptr(const void* p, const char* what, bool allow_null);
+
+}  // namespace fea
+
+extern "C" int fea_log_f64(const double* x, double* y, int64_t n, void* stream) {
+  if (n < 0) return fea::set_error(FEA_EINVAL, "negative length");
+  if (n == 0) return FEA_OK;
+  int rc;
+  if ((rc = fea::check_device_ptr(x, "x", false))) return rc;
+  if ((rc = fea::check_device_ptr(y, "y", false))) return rc;
+  const int64_t grid = std::min<int64_t>((n + 255) / 256, 152 * 8);  // grid-stride: any grid covers n
+  fea::log_f64_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fea::set_error(FEA_ECUDA, cudaGetErrorString(e));
+  return FEA_OK;
+}

@@ -18,6 +18,7 @@
 //   D[c,I][d,J] = s (mu d_cd d_IJ + (mu - lam ln J) Fi_Jc Fi_Id + lam Fi_Ic Fi_Jd).
 #pragma once
 #include "common.cuh"
+#include "log_f64.cuh"
 
 namespace fea {
 
@@ -137,7 +138,7 @@ struct SeTile {
         T* o = DF + 12 * w;
 #pragma unroll
         for (int k = 0; k < 9; ++k) o[k] = bad ? nan : from_double<T>(cof[k] * idF);
-        o[9] = bad ? nan : from_double<T>(log(dF));
+        o[9] = bad ? nan : from_double<T>(log_f64(dF));
       }
       __syncthreads();
     }

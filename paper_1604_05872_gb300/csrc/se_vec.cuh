@@ -34,6 +34,7 @@
 // which are dead once the last point group has been accumulated.
 #pragma once
 #include "common.cuh"
+#include "log_f64.cuh"
 #include "sym.cuh"
 
 namespace fea {
@@ -207,7 +208,7 @@ struct SeVecTile {
         // the cancellation-prone cofactors and det F are FP64; the division by
         // det F is a well-conditioned scaling done after rounding to T
         const T idF = T(1) / from_double<T>(dF);
-        const T lnJ = from_double<T>(log(dF));
+        const T lnJ = from_double<T>(log_f64(dF));
         const T smu = s * mu_c;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {

@@ -17,6 +17,7 @@
 // entries and set the error word.
 #pragma once
 #include "common.cuh"
+#include "log_f64.cuh"
 
 namespace fea {
 
@@ -174,7 +175,7 @@ struct ResVecTile {
       const bool bad = !(dF > 0.0) || !isfinite(dF);
       if (bad) flag_error(err, ERR_DEGENERATE);
       const T idF = T(1) / from_double<T>(dF);
-      const T lnJ = from_double<T>(log(dF));
+      const T lnJ = from_double<T>(log_f64(dF));
       const T s = Wt[qq] * Ji[9];
       // P = mu (F - F^-T) + lam lnJ F^-T with F - F^-T = grad u + F^-T grad u^T
       // (I - F^-T = F^-T (F^T - I)): no cancellation for small displacements.

@@ -82,11 +82,15 @@ def test_gpu_global_assembly_matches_reference(fea, orc, form, p):
     ref_elem = orc.assemble(form, p, coords, coeffs)
     _, _, ref = global_ref.assemble_csr(d, ref_elem, nrows)
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
-    # the two-step form (positions once, then search-free scatter) gives the same sums
+    # the two-step form (positions once, then search-free scatter) gives the same sums, with
+    # 4- and 8-byte maps holding the same positions
     smap = fea.csr_scatter_map(dd, rp, ci)
-    vals_m = fea.scatter_add_csr_mapped(smap, elem, torch.zeros_like(vals))
-    fea.sync()
-    assert torch.allclose(vals_m, vals, rtol=0, atol=1e-12 * float(vals.abs().max()))
+    smap64 = fea.csr_scatter_map(dd, rp, ci, index_dtype=torch.int64)
+    assert smap.dtype == torch.int32 and torch.equal(smap.long(), smap64)
+    for m in (smap, smap64):
+        vals_m = fea.scatter_add_csr_mapped(m, elem, torch.zeros_like(vals))
+        fea.sync()
+        assert torch.allclose(vals_m, vals, rtol=0, atol=1e-12 * float(vals.abs().max()))
     # FP32 element input gives the same sums of the rounded values
     vals32 = torch.zeros_like(vals)
     fea.scatter_add_csr(dd, fea.assemble(form, p, c, f, out_f32=True), rp, ci, vals32)
@@ -107,6 +111,15 @@ def test_gpu_scatter_outside_pattern_is_flagged(fea):
     with pytest.raises(fea.FeaError) as ei:
         fea.sync()
     assert ei.value.code == fea.EINVAL
+    # the mapped form: missing entries map to -1 and are flagged at both steps
+    dd = torch.from_numpy(dofs).cuda()
+    smap = fea.csr_scatter_map(dd, torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col_idx).cuda())
+    with pytest.raises(fea.FeaError):
+        fea.sync()
+    assert int((smap < 0).sum()) == smap.numel() - dofs.size  # only the diagonal entries are in the pattern
+    fea.scatter_add_csr_mapped(smap, elem, vals)
+    with pytest.raises(fea.FeaError):
+        fea.sync()
     bad = dofs.copy()
     bad[3, 2] = nd + 5  # a DOF outside the rows: skipped on the device, flagged
     fea.scatter_add_csr(torch.from_numpy(bad).cuda(), elem, torch.from_numpy(row_ptr).cuda(),
