@@ -198,6 +198,20 @@ int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_t nrows, co
 int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, const void* elem, int elem_f32,
                                int64_t nnz, double* values, void* stream);
 
+/* Local and global assembly in one pass: for mass and Helmholtz P1-P3 the
+ * streaming pre-evaluated kernel adds every element matrix entry into the CSR
+ * values at its position instead of storing the matrix: values[map[e][i][j]]
+ * += A_e[i][j] (DEVICE arrays, on `stream`; coords and coeffs as for
+ * fea_assemble; map [E][n][n] from fea_csr_scatter_map, int32 when map_i64 = 0
+ * (nnz < 2^31) or int64; values [nnz] double, accumulated into).  FP32
+ * contraction, FP64 atomics (the last bits of the sums vary between runs).
+ * FEA_EINVAL for other forms and degrees (use fea_assemble, then
+ * fea_scatter_add_csr_mapped); a position outside [0, nnz) is skipped and
+ * makes the next fea_sync return FEA_EINVAL; a degenerate element adds NaN and
+ * makes it return FEA_EDEGENERATE. */
+int fea_assemble_csr(int form, int degree, int64_t E, const double* coords, const double* coeffs,
+                     const void* map, int map_i64, int64_t nnz, double* values, void* stream);
+
 /* Uneven batch of requests (forms, degrees and sizes mixed) in one CUDA graph
  * launch, captured once per distinct batch and replayed: each request runs the
  * persistent kernel it would run alone (its own tile, registers and shared

@@ -24,7 +24,7 @@ VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
            "fea_assemble_vector", "fea_csr_pattern", "fea_scatter_add_csr",
-           "fea_csr_scatter_map", "fea_scatter_add_csr_mapped", "fea_log_f64",
+           "fea_csr_scatter_map", "fea_scatter_add_csr_mapped", "fea_assemble_csr", "fea_log_f64",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_fused",
            "fea_assemble_batch_noalloc",
            "fea_sync", "fea_plan", "fea_plan_flop",
@@ -87,6 +87,7 @@ def load(path=None):
     lib.fea_scatter_add_csr.argtypes = [i64, i, vp, vp, i, i64, vp, vp, i64, vp, vp]
     lib.fea_csr_scatter_map.argtypes = [i64, i, vp, i64, vp, vp, i64, vp, i, vp]
     lib.fea_log_f64.argtypes = [vp, vp, i64, vp]
+    lib.fea_assemble_csr.argtypes = [i, i, i64, vp, vp, vp, i, i64, vp, vp]
     lib.fea_scatter_add_csr_mapped.argtypes = [i64, i, vp, i, vp, i, i64, vp, vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
@@ -246,6 +247,18 @@ def csr_scatter_map(dofs, row_ptr, col_idx, stream=None, index_dtype=None):
     _check(load().fea_csr_scatter_map(E, n, _ptr(dofs), row_ptr.shape[0] - 1, _ptr(row_ptr), _ptr(col_idx),
                                       nnz, _ptr(m), int(index_dtype == torch.int64), _stream_ptr(stream)))
     return m
+
+
+def assemble_csr(form, degree, coords, coeffs, scatter_map, values, stream=None):
+    """Local and global assembly in one pass (mass, Helmholtz P1-P3): values[map] += A_e, the
+    element matrices never stored; fea_assemble_csr.  Returns `values`."""
+    import torch
+    if scatter_map.dtype not in (torch.int32, torch.int64):
+        raise TypeError("scatter map must be int32 or int64")
+    _check(load().fea_assemble_csr(form, degree, coords.shape[0], _ptr(coords), _ptr(coeffs),
+                                   _ptr(scatter_map), int(scatter_map.dtype == torch.int64), values.shape[0],
+                                   _ptr(values), _stream_ptr(stream)))
+    return values
 
 
 def log_f64(x, stream=None):

@@ -84,6 +84,7 @@ __device__ __forceinline__ void flag_error(unsigned* err, unsigned code) {
   if (err) atomicOr(err, code);
 }
 constexpr unsigned ERR_DEGENERATE = 1u;
+constexpr unsigned ERR_PATTERN = 8u;  // a global-assembly position outside the CSR pattern
 
 // ----------------------------------------------------------------------------
 // Tile input: copy `n` doubles from global (8-byte aligned start) to shared

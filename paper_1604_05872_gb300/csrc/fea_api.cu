@@ -311,6 +311,63 @@ int assemble_impl(int form, int degree, int64_t E, const double* coords, const d
   return launch_plan(st, pl, form, degree, E, coords, coeffs, out, o.out_f32, (cudaStream_t)stream);
 }
 
+// Local and global assembly in one pass: the streaming pre-evaluated kernel
+// adds each element matrix into the CSR values at its precomputed positions
+// instead of storing it (mass and Helmholtz P1-P3, FP32 contraction).
+int assemble_csr_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs, const void* map,
+                      int map_i64, int64_t nnz, double* values, void* stream) {
+  if (!valid_fd(form, degree)) return fail(FEA_EINVAL, "unsupported form/degree");
+  if ((form != FEA_MASS && form != FEA_HELMHOLTZ) || degree > 3)
+    return fail(FEA_EINVAL, "one-pass global assembly covers mass and Helmholtz P1-P3 "
+                            "(other forms: fea_assemble, then fea_scatter_add_csr_mapped)");
+  if (E < 0 || nnz < 0) return fail(FEA_EINVAL, "negative size");
+  if (map_i64 != 0 && map_i64 != 1) return fail(FEA_EINVAL, "map_i64 must be 0 or 1");
+  if (!map_i64 && nnz > 2147483647) return fail(FEA_EINVAL, "nnz >= 2^31 needs an int64 map");
+  const int n = local_dim(form, degree);
+  if (E > (int64_t)(INT64_MAX / ((int64_t)n * n * 8))) return fail(FEA_EINVAL, "size overflow");
+  DevState* st = nullptr;
+  int rc = get_dev(&st);
+  if (rc) return rc;
+  fea_options o = default_options();
+  o.variant = FEA_VARIANT_PRE;
+  Plan pl;
+  if ((rc = make_plan(st, form, degree, o, &pl, false))) return rc;
+  const void* fn = find_scatter_kernel(pl.k->fn, map_i64);
+  if (!fn) return fail(FEA_EINVAL, "no one-pass kernel for this plan");
+  if (E == 0) return FEA_OK;
+  if ((rc = check_device_ptr(coords, "coords", false))) return rc;
+  if ((rc = check_device_ptr(coeffs, "coeffs", form == FEA_MASS))) return rc;
+  if ((rc = check_device_ptr(map, "map", false))) return rc;
+  if ((rc = check_device_ptr(values, "values", nnz == 0))) return rc;
+  PreparedLaunch L;
+  if ((rc = prepare_launch(st, pl, form, degree, E, coords, coeffs, nullptr, 0, &L))) return rc;
+  int per_sm = 0;
+  {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, size_t, int>, int> occ;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(fn, pl.smem, st->dev);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+      cudaFuncAttributes fa;
+      CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+      CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)st->smem_optin - (int)fa.sharedSizeBytes));
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, pl.smem));
+      occ[key] = per_sm;
+    } else {
+      per_sm = it->second;
+    }
+  }
+  if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with this tile");
+  const int64_t ntiles = (E + pl.tile - 1) / pl.tile;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
+  ScatterArgs sc{map, nnz, values};
+  void* args[] = {&L.q, &sc, &L.err};
+  CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, pl.smem, (cudaStream_t)stream));
+  return FEA_OK;
+}
+
 // Element vectors (linear forms): Helmholtz load vector, Neo-Hookean residual.
 int assemble_vector_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
                          const fea_options* opt, void* stream) {
@@ -495,6 +552,10 @@ int fea_assemble_vector(int form, int degree, int64_t E, const double* coords, c
 }
 int fea_assemble_batch_fused(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   return batch_fused_impl(reqs, nreq, opt, stream);
+}
+int fea_assemble_csr(int form, int degree, int64_t E, const double* coords, const double* coeffs, const void* map,
+                     int map_i64, int64_t nnz, double* values, void* stream) {
+  return assemble_csr_impl(form, degree, E, coords, coeffs, map, map_i64, nnz, values, stream);
 }
 int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   return batch_noalloc_impl(reqs, nreq, opt, stream);

@@ -21,8 +21,6 @@
 
 namespace fea {
 
-constexpr unsigned ERR_PATTERN = 8u;
-
 template <typename TE>
 __global__ void __launch_bounds__(256) scatter_csr_kernel(int64_t E, int n, const int32_t* __restrict__ dofs,
                                                           const TE* __restrict__ elem, int64_t nrows,

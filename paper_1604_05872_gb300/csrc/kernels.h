@@ -33,5 +33,8 @@ const KernelInfo* find_kernel(int variant, int form, int p, int prec, size_t bud
 const KernelInfo* find_batch_kernel(int variant, int form, int p);
 // Element-vector kernels (linear forms): Helmholtz load vector, Neo-Hookean residual.
 const KernelInfo* find_vec_kernel(int form, int p, int prec);
+// The fused local + global assembly form of the streaming kernel `plain`
+// (mass and Helmholtz P1-P3), with an int32 or int64 position map; nullptr if none.
+const void* find_scatter_kernel(const void* plain, int map_i64);
 
 }  // namespace fea

@@ -37,6 +37,27 @@ const KernelInfo kPreKernels[] = {
 #undef PREVS
 const int kNumPreKernels = sizeof(kPreKernels) / sizeof(kPreKernels[0]);
 
+// Local and global assembly in one pass (the streaming kernel adding into CSR
+// values): the plain streaming kernel it replaces and its int32 / int64 map forms.
+struct ScatterKernel {
+  int form, p;
+  const void* plain;
+  const void* map32;
+  const void* map64;
+};
+#define SCAT(F, P)                                                                                      \
+  ScatterKernel{F, P, reinterpret_cast<const void*>(&pre_stream_kernel<F, P>),                          \
+                reinterpret_cast<const void*>(&pre_stream_scatter_kernel<F, P, 4>),                     \
+                reinterpret_cast<const void*>(&pre_stream_scatter_kernel<F, P, 8>)}
+const ScatterKernel kScatterKernels[] = {SCAT(0, 1), SCAT(0, 2), SCAT(0, 3), SCAT(1, 1), SCAT(1, 2), SCAT(1, 3)};
+#undef SCAT
+
+const void* find_scatter_kernel(const void* plain, int map_i64) {
+  for (const ScatterKernel& k : kScatterKernels)
+    if (k.plain == plain) return map_i64 ? k.map64 : k.map32;
+  return nullptr;
+}
+
 // The FP32 tile functions the batched kernel dispatches to (their shared-memory
 // layouts and tile limits plan the batch).
 #define PT(F, P) make_info<PreTile<F, P, float>>(V_PRE, F, P, 1)

@@ -59,6 +59,14 @@ struct Req {
   int64_t tile0;     // first global tile of this request (batch)
 };
 
+// Global assembly target of the one-pass kernel: the CSR values of the global
+// matrix and, per element entry (e, i, j), its position in them (int32 or int64).
+struct ScatterArgs {
+  const void* map;
+  int64_t nnz;
+  double* values;
+};
+
 enum Variant { V_NAIVE = 0, V_SE = 1, V_PRE = 2 };
 
 }  // namespace fea

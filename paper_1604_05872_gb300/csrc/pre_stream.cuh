@@ -14,6 +14,12 @@
 //     16-byte aligned).
 // Every mbarrier wait is bounded; a wait that gives up sets the error word and
 // the whole CTA leaves the kernel.
+//
+// The same schedule also serves local and global assembly in one pass
+// (pre_stream_scatter_kernel): instead of storing the pair of entries, the
+// thread adds them into the CSR values of the global matrix at the positions
+// map[e][i][j] (one 8- or 16-byte map load per pair, two FP64 atomics), so the
+// element matrices never reach HBM.
 #pragma once
 #include "common.cuh"
 
@@ -120,8 +126,30 @@ __device__ __forceinline__ double f2d_finite(float f) {
   return __hiloint2double((int)hi, (int)(a << 29));
 }
 
-template <int FORM, int P>
-__global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
+// The fused global assembly adds values[map[e][i][j]] += A_e[i][j] (ScatterArgs),
+// map int32 (MAPW 4) or int64 (MAPW 8); positions outside [0, nnz) are skipped
+// and flagged.
+template <int MAPW>
+__device__ __forceinline__ void scatter_pair(const ScatterArgs& sc, int64_t k, double v0, double v1, unsigned* err) {
+  int64_t m0, m1;
+  if constexpr (MAPW == 4) {
+    const int2 m = __ldg(reinterpret_cast<const int2*>(static_cast<const int32_t*>(sc.map) + k));
+    m0 = m.x;
+    m1 = m.y;
+  } else {
+    const longlong2 m = __ldg(reinterpret_cast<const longlong2*>(static_cast<const int64_t*>(sc.map) + k));
+    m0 = m.x;
+    m1 = m.y;
+  }
+  if (m0 >= 0 && m0 < sc.nnz) atomicAdd(sc.values + m0, v0);
+  else flag_error(err, ERR_PATTERN);
+  if (m1 >= 0 && m1 < sc.nnz) atomicAdd(sc.values + m1, v1);
+  else flag_error(err, ERR_PATTERN);
+}
+
+// MAPW 0: store the element matrices; 4 or 8: add them into the CSR values.
+template <int FORM, int P, int MAPW>
+__device__ __forceinline__ void pre_stream_body(const Req& q, unsigned* err, const ScatterArgs& sc) {
   using K = PreStream<FORM, P>;
   extern __shared__ __align__(16) char sm[];
   const int TE = q.tile;
@@ -241,7 +269,12 @@ __global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
               b1 = fmaf(r1[r4 + k], gg[k], b1);
             }
         }
-        if (q.out_f32) {
+        if constexpr (MAPW != 0) {
+          const double2 v = h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1));
+          const double2 w = h2[0] != h2[0] ? nan2 : make_double2(f2d_finite(b0), f2d_finite(b1));
+          scatter_pair<MAPW>(sc, (e0 + e) * K::NN + 2 * slot, v.x, v.y, err);
+          scatter_pair<MAPW>(sc, (e0 + e + K::G) * K::NN + 2 * slot, w.x, w.y, err);
+        } else if (q.out_f32) {
           __stcs(of + (size_t)e * (K::NN / 2), make_float2(a0, a1));
           __stcs(of + (size_t)(e + K::G) * (K::NN / 2), make_float2(b0, b1));
         } else {
@@ -265,7 +298,10 @@ __global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
               a1 = fmaf(r1[r4 + k], hh[k], a1);
             }
         }
-        if (q.out_f32) {
+        if constexpr (MAPW != 0) {
+          const double2 v = h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1));
+          scatter_pair<MAPW>(sc, (e0 + e) * K::NN + 2 * slot, v.x, v.y, err);
+        } else if (q.out_f32) {
           __stcs(of + (size_t)e * (K::NN / 2), make_float2(a0, a1));
         } else {
           __stcs(o + (size_t)e * (K::NN / 2), h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1)));
@@ -288,6 +324,16 @@ __global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
       return;
     }
   }
+}
+
+template <int FORM, int P>
+__global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
+  pre_stream_body<FORM, P, 0>(q, err, ScatterArgs{nullptr, 0, nullptr});
+}
+
+template <int FORM, int P, int MAPW>
+__global__ void __launch_bounds__(NT) pre_stream_scatter_kernel(Req q, ScatterArgs sc, unsigned* err) {
+  pre_stream_body<FORM, P, MAPW>(q, err, sc);
 }
 
 }  // namespace fea

@@ -93,3 +93,12 @@ def test_scatter_argument_checks_without_gpu(lib):
     assert lib.fea_csr_scatter_map(10, 4, nul, 5, nul, nul, 100, nul, 2, nul) == fea.EINVAL
     assert lib.fea_scatter_add_csr_mapped(10, 4, nul, 3, nul, 0, 100, nul, nul) == fea.EINVAL
     assert lib.fea_scatter_add_csr_mapped(-1, 4, nul, 0, nul, 0, 100, nul, nul) == fea.EINVAL
+
+
+def test_one_pass_global_assembly_argument_checks_without_gpu(lib):
+    nul = ctypes.c_void_p(0)
+    for form, p, nnz, w in ((2, 1, 100, 0), (3, 2, 100, 0), (0, 4, 100, 0), (1, 1, 2 ** 31, 0), (0, 1, 100, 3),
+                            (0, 1, -1, 0)):
+        assert lib.fea_assemble_csr(form, p, 10, nul, nul, nul, w, nnz, nul, nul) == fea.EINVAL, (form, p, nnz, w)
+    lib.fea_assemble_csr(2, 1, 10, nul, nul, nul, 0, 100, nul, nul)
+    assert "one-pass" in lib.fea_last_error().decode()

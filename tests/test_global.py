@@ -126,3 +126,75 @@ def test_gpu_scatter_outside_pattern_is_flagged(fea):
                         torch.from_numpy(col_idx).cuda(), vals)
     with pytest.raises(fea.FeaError):
         fea.sync()
+
+
+def random_dof_map(E, n, ndofs, rng):
+    """An element-to-DOF map with distinct DOFs per element (any degree; no mesh needed)."""
+    return np.stack([rng.choice(ndofs, size=n, replace=False) for _ in range(E)]).astype(np.int32)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form,p,mesh", [(0, 1, True), (1, 1, True), (1, 2, True), (0, 2, True),
+                                         (1, 3, False), (0, 3, False)])
+@pytest.mark.parametrize("index_dtype", ["int32", "int64"])
+def test_gpu_one_pass_global_assembly(fea, orc, form, p, mesh, index_dtype):
+    """fea_assemble_csr (element matrices added into the CSR values, never stored) against the
+    two-pass form on the same inputs (summation order only) and against the reference global
+    matrix of the oracle's element matrices (the FP32 contraction's tolerance)."""
+    import torch
+    rng = np.random.default_rng(11 + p)
+    if mesh:
+        coords, dofs, nd = inputs.box_mesh(6, p, jitter=0.1)  # 1296 elements, a ragged last tile
+    else:
+        E, n = 1111, fea.local_dim(form, p)
+        coords, _ = inputs.workload(form, p, E, seed=inputs.SEED + 31)
+        nd = 3000
+        dofs = random_dof_map(E, n, nd, rng)
+    E = coords.shape[0]
+    coeffs = None if form == 0 else inputs.random_coeffs(form, p, E, rng)
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd)
+    c = torch.from_numpy(coords).cuda()
+    f = None if coeffs is None else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
+    dd, rp, ci = (torch.from_numpy(x).cuda() for x in (dofs, row_ptr, col_idx))
+    smap = fea.csr_scatter_map(dd, rp, ci, index_dtype=getattr(torch, index_dtype))
+    vals = fea.assemble_csr(form, p, c, f, smap, torch.zeros(col_idx.shape[0], dtype=torch.float64, device="cuda"))
+    two = fea.scatter_add_csr_mapped(smap, fea.assemble(form, p, c, f), torch.zeros_like(vals))
+    fea.sync()
+    assert torch.allclose(vals, two, rtol=0, atol=1e-12 * float(two.abs().max()))
+    ref_elem = orc.assemble(form, p, coords, coeffs)
+    _, _, ref = global_ref.assemble_csr(dofs, ref_elem, nd)
+    got = vals.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    # accumulation: a second pass doubles the matrix
+    fea.assemble_csr(form, p, c, f, smap, vals)
+    fea.sync()
+    assert torch.allclose(vals, 2 * two, rtol=0, atol=1e-12 * float(two.abs().max()))
+
+
+@pytest.mark.gpu
+def test_gpu_one_pass_rejects_and_flags(fea):
+    import torch
+    coords, dofs, nd = inputs.box_mesh(2, 1)
+    c = torch.from_numpy(coords).cuda()
+    dd = torch.from_numpy(dofs).cuda()
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd)
+    smap = fea.csr_scatter_map(dd, torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col_idx).cuda())
+    vals = torch.zeros(col_idx.shape[0], dtype=torch.float64, device="cuda")
+    fea.sync()
+    with pytest.raises(fea.FeaError) as e:  # no one-pass kernel for the vector forms
+        fea.assemble_csr(2, 1, c, torch.zeros(c.shape[0] * 8, dtype=torch.float64, device="cuda"), smap, vals)
+    assert e.value.code == fea.EINVAL
+    with pytest.raises(fea.FeaError):  # nor for P4
+        fea.assemble_csr(0, 4, c, None, smap, vals)
+    bad = smap.clone()
+    bad[5, 1, 2] = col_idx.shape[0] + 7  # a position outside the values: skipped, flagged
+    bad[9, 0, 0] = -3
+    fea.assemble_csr(0, 1, c, None, bad, vals)
+    with pytest.raises(fea.FeaError) as e:
+        fea.sync()
+    assert e.value.code == fea.EINVAL
+    # every other entry was added: the sum of all element entries (the cube's volume up to the
+    # FP32 contraction's rounding) minus the two skipped ones
+    m = fea.assemble(0, 1, c).cpu().numpy()
+    assert abs(m.sum() - 1.0) < 1e-6
+    assert abs(float(vals.sum()) - (m.sum() - m[5, 1, 2] - m[9, 0, 0])) < 1e-13
