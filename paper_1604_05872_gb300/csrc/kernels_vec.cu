@@ -3,14 +3,25 @@
 
 #include "../../include/fea.h"
 #include "launch.cuh"
+#include "pre_stream.cuh"
 #include "vec_forms.cuh"
 
 namespace fea {
 
+// the streaming load-vector kernel (P1-P3, FP32) ahead of the tile kernel it replaces
+template <int P>
+size_t load_stream_smem(int TE, int Q) { return PreStreamLoad<P>::smem(TE, Q); }
+template <int P>
+KernelInfo load_stream_info() {
+  return KernelInfo{reinterpret_cast<const void*>(&pre_stream_load_kernel<P>), V_PRE, 1, P, 1, NT, &load_stream_smem<P>,
+                    128};
+}
 #define LV(P) make_info<LoadVecTile<P, float>>(V_PRE, 1, P, 1), make_info<LoadVecTile<P, double>>(V_PRE, 1, P, 0)
+#define LVS(P) load_stream_info<P>(), LV(P)
 #define RV(P) make_info<ResVecTile<P, float>>(V_SE, 3, P, 1), make_info<ResVecTile<P, double>>(V_SE, 3, P, 0)
-const KernelInfo kVecKernels[] = {LV(1), LV(2), LV(3), LV(4), RV(1), RV(2), RV(3), RV(4)};
+const KernelInfo kVecKernels[] = {LVS(1), LVS(2), LVS(3), LV(4), RV(1), RV(2), RV(3), RV(4)};
 #undef LV
+#undef LVS
 #undef RV
 const int kNumVecKernels = sizeof(kVecKernels) / sizeof(kVecKernels[0]);
 

@@ -77,6 +77,9 @@ struct PreStream {
   static constexpr int S = NN / 2;                 // pair slots
   static constexpr int G = S >= NT ? 1 : NT / S;   // element groups
   static constexpr int IN = 12 + CLEN;             // doubles of input per element
+  static constexpr int NOUT = NN;                  // output entries per element
+  static constexpr int RTAB = R;                   // terms of the device table
+  static constexpr int RSTRIDE = NN;               // floats between consecutive terms of R
 
   FEA_HD static size_t off_h(int TE) { return round_up_sz((size_t)2 * TE * IN * 8, 16); }
   FEA_HD static size_t off_bar(int TE) { return off_h(TE) + round_up_sz((size_t)2 * TE * NHP * 4, 16); }
@@ -117,6 +120,55 @@ struct PreStream {
   }
 };
 
+// The Helmholtz load vector b_e = |det J| M f_e (mass reference matrix M =
+// int phi_i phi_k, the mass form's one-term table; P1-P3, NS even) on the same
+// schedule: the "terms" are the NS coefficient DOFs, the geometry tensor is
+// |det J| f_e (FP64 det J, FP32 product), each thread holds two rows of M.
+template <int P>
+struct PreStreamLoad {
+  static constexpr int NS = nbasis_c(P);
+  static_assert(NS % 2 == 0, "even entry count");
+  static constexpr int NOUT = NS;
+  static constexpr int R = NS;
+  static constexpr int NHP = round_up(R, 4);
+  static constexpr int CLEN = NS;
+  static constexpr int S = NOUT / 2;
+  static constexpr int G = S >= NT ? 1 : NT / S;
+  static constexpr int IN = 12 + CLEN;
+  static constexpr int RTAB = 1;
+  static constexpr int RSTRIDE = NS;  // M is symmetric: term k of the pair (i, i + 1) is M[k][i], M[k][i + 1]
+
+  FEA_HD static size_t off_h(int TE) { return round_up_sz((size_t)2 * TE * IN * 8, 16); }
+  FEA_HD static size_t off_bar(int TE) { return off_h(TE) + round_up_sz((size_t)2 * TE * NHP * 4, 16); }
+  FEA_HD static size_t smem(int TE, int Q) { (void)Q; return off_bar(TE) + 16 + 16; }
+  FEA_HD static int max_tile() { return NT; }
+
+  __device__ static void geometry_h(const double* x, const double* c, float* h, unsigned* err) {
+    double J[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) J[r][k] = x[3 * (k + 1) + r] - x[r];
+    const double det = fma(J[0][0], fma(J[1][1], J[2][2], -J[1][2] * J[2][1]),
+                           fma(J[0][1], fma(J[1][2], J[2][0], -J[1][0] * J[2][2]),
+                               J[0][2] * fma(J[1][0], J[2][1], -J[1][1] * J[2][0])));
+    const uint64_t bits = (uint64_t)__double_as_longlong(det);
+    const bool bad = ((bits << 1) == 0) || ((bits >> 52 & 0x7ff) == 0x7ff);  // zero, inf or NaN
+    if (bad) flag_error(err, ERR_DEGENERATE);
+    const float ad = __uint_as_float(__float_as_uint(d2f(det)) & 0x7fffffffu);
+    const float nan = __int_as_float(0x7fc00000);
+    float v[NHP];
+#pragma unroll
+    for (int k = 0; k < NHP; ++k) v[k] = k < NS ? ad * d2f(c[k]) : 0.f;
+#pragma unroll
+    for (int k = 0; k < NHP; k += 4) {
+      float4 w;
+      w.x = bad ? nan : v[k]; w.y = bad ? nan : v[k + 1]; w.z = bad ? nan : v[k + 2]; w.w = bad ? nan : v[k + 3];
+      *reinterpret_cast<float4*>(h + k) = w;
+    }
+  }
+};
+
 // Exact widening of a finite float that is normal or zero (no subnormals arise
 // under flush-to-zero); NaN rows of degenerate elements are written separately.
 __device__ __forceinline__ double f2d_finite(float f) {
@@ -148,16 +200,15 @@ __device__ __forceinline__ void scatter_pair(const ScatterArgs& sc, int64_t k, d
 }
 
 // MAPW 0: store the element matrices; 4 or 8: add them into the CSR values.
-template <int FORM, int P, int MAPW>
+template <class K, int MAPW>
 __device__ __forceinline__ void pre_stream_body(const Req& q, unsigned* err, const ScatterArgs& sc) {
-  using K = PreStream<FORM, P>;
   extern __shared__ __align__(16) char sm[];
   const int TE = q.tile;
   double* in = reinterpret_cast<double*>(sm);                 // [2][TE][IN]: coords block, then coeffs block
   float* H = reinterpret_cast<float*>(sm + K::off_h(TE));      // [2][TE][NHP]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + K::off_bar(TE));
   __shared__ int s_abort;
-  const TabLayout L = tab_layout(q.Q, K::NS, K::R);
+  const TabLayout L = tab_layout(q.Q, K::NS, K::RTAB);
   const float* Rg = reinterpret_cast<const float*>(q.tab) + L.offR;
   const int64_t ntiles = (q.E + TE - 1) / TE;
   const int64_t first = blockIdx.x;
@@ -240,13 +291,13 @@ __device__ __forceinline__ void pre_stream_body(const Req& q, unsigned* err, con
       float r0[K::R], r1[K::R];
 #pragma unroll
       for (int r = 0; r < K::R; ++r) {
-        const float2 x = __ldg(reinterpret_cast<const float2*>(Rg + (size_t)r * K::NN) + slot);
+        const float2 x = __ldg(reinterpret_cast<const float2*>(Rg + (size_t)r * K::RSTRIDE) + slot);
         r0[r] = x.x;
         r1[r] = x.y;
       }
       const float* Hb = H + (size_t)(j & 1) * TE * K::NHP;
-      double2* o = reinterpret_cast<double2*>(reinterpret_cast<double*>(q.out) + e0 * K::NN) + slot;
-      float2* of = reinterpret_cast<float2*>(reinterpret_cast<float*>(q.out) + e0 * K::NN) + slot;
+      double2* o = reinterpret_cast<double2*>(reinterpret_cast<double*>(q.out) + e0 * K::NOUT) + slot;
+      float2* of = reinterpret_cast<float2*>(reinterpret_cast<float*>(q.out) + e0 * K::NOUT) + slot;
       const double2 nan2 = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
       // two elements per iteration: independent accumulation chains
       int e = g0;
@@ -272,16 +323,16 @@ __device__ __forceinline__ void pre_stream_body(const Req& q, unsigned* err, con
         if constexpr (MAPW != 0) {
           const double2 v = h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1));
           const double2 w = h2[0] != h2[0] ? nan2 : make_double2(f2d_finite(b0), f2d_finite(b1));
-          scatter_pair<MAPW>(sc, (e0 + e) * K::NN + 2 * slot, v.x, v.y, err);
-          scatter_pair<MAPW>(sc, (e0 + e + K::G) * K::NN + 2 * slot, w.x, w.y, err);
+          scatter_pair<MAPW>(sc, (e0 + e) * K::NOUT + 2 * slot, v.x, v.y, err);
+          scatter_pair<MAPW>(sc, (e0 + e + K::G) * K::NOUT + 2 * slot, w.x, w.y, err);
         } else if (q.out_f32) {
-          __stcs(of + (size_t)e * (K::NN / 2), make_float2(a0, a1));
-          __stcs(of + (size_t)(e + K::G) * (K::NN / 2), make_float2(b0, b1));
+          __stcs(of + (size_t)e * (K::NOUT / 2), make_float2(a0, a1));
+          __stcs(of + (size_t)(e + K::G) * (K::NOUT / 2), make_float2(b0, b1));
         } else {
           const double2 v = h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1));
           const double2 w = h2[0] != h2[0] ? nan2 : make_double2(f2d_finite(b0), f2d_finite(b1));
-          __stcs(o + (size_t)e * (K::NN / 2), v);
-          __stcs(o + (size_t)(e + K::G) * (K::NN / 2), w);
+          __stcs(o + (size_t)e * (K::NOUT / 2), v);
+          __stcs(o + (size_t)(e + K::G) * (K::NOUT / 2), w);
         }
       }
       for (; e < ne; e += K::G) {
@@ -300,11 +351,11 @@ __device__ __forceinline__ void pre_stream_body(const Req& q, unsigned* err, con
         }
         if constexpr (MAPW != 0) {
           const double2 v = h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1));
-          scatter_pair<MAPW>(sc, (e0 + e) * K::NN + 2 * slot, v.x, v.y, err);
+          scatter_pair<MAPW>(sc, (e0 + e) * K::NOUT + 2 * slot, v.x, v.y, err);
         } else if (q.out_f32) {
-          __stcs(of + (size_t)e * (K::NN / 2), make_float2(a0, a1));
+          __stcs(of + (size_t)e * (K::NOUT / 2), make_float2(a0, a1));
         } else {
-          __stcs(o + (size_t)e * (K::NN / 2), h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1)));
+          __stcs(o + (size_t)e * (K::NOUT / 2), h[0] != h[0] ? nan2 : make_double2(f2d_finite(a0), f2d_finite(a1)));
         }
       }
     }
@@ -328,12 +379,17 @@ __device__ __forceinline__ void pre_stream_body(const Req& q, unsigned* err, con
 
 template <int FORM, int P>
 __global__ void __launch_bounds__(NT) pre_stream_kernel(Req q, unsigned* err) {
-  pre_stream_body<FORM, P, 0>(q, err, ScatterArgs{nullptr, 0, nullptr});
+  pre_stream_body<PreStream<FORM, P>, 0>(q, err, ScatterArgs{nullptr, 0, nullptr});
 }
 
 template <int FORM, int P, int MAPW>
 __global__ void __launch_bounds__(NT) pre_stream_scatter_kernel(Req q, ScatterArgs sc, unsigned* err) {
-  pre_stream_body<FORM, P, MAPW>(q, err, sc);
+  pre_stream_body<PreStream<FORM, P>, MAPW>(q, err, sc);
+}
+
+template <int P>
+__global__ void __launch_bounds__(NT) pre_stream_load_kernel(Req q, unsigned* err) {
+  pre_stream_body<PreStreamLoad<P>, 0>(q, err, ScatterArgs{nullptr, 0, nullptr});
 }
 
 }  // namespace fea

@@ -77,3 +77,22 @@ def test_vector_degenerate_element_is_nan(fea):
     assert ei.value.code == fea.EDEGENERATE
     o = out.cpu().numpy()
     assert np.isnan(o[7]).all() and np.isfinite(np.delete(o, 7, axis=0)).all()
+
+
+def test_load_vector_many_tiles_per_cta_and_degenerate(fea, orc):
+    """More tiles than resident CTAs (each CTA streams several, double-buffered), a ragged tail and
+    one collapsed element: its row is NaN and flagged, every other row matches the oracle."""
+    import torch
+    E = 152 * 8 * 128 + 77
+    coords, f, c, fd = _data(inputs.HELMHOLTZ, 2, E, seed=240)
+    coords[E - 5, 2] = coords[E - 5, 0]
+    c = torch.from_numpy(coords).cuda()
+    out = fea.assemble_vector(fea.HELMHOLTZ, 2, c, fd)
+    with pytest.raises(fea.FeaError) as ei:
+        fea.sync()
+    assert ei.value.code == fea.EDEGENERATE
+    o = out.cpu().numpy()
+    assert np.isnan(o[E - 5]).all()
+    keep = np.ones(E, dtype=bool)
+    keep[E - 5] = False
+    assert _rel(o[keep], orc.load_vector(2, coords[keep], f[keep])) <= 1e-5
