@@ -54,6 +54,10 @@ PROFILES = {
                            ["common.cuh", "layout.h", "launch.cuh", "se_vec.cuh", "sym.cuh", "log_f64.cuh",
                             "log_table.h", "planner.cpp"]),
     "helmholtz_p2_global_1M": ("global_helmholtz_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh", "planner.cpp"]),
+    "helmholtz_load_p2_1M": ("helmholtz_load_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh"]),
+    "neohookean_residual_p2_500k": ("neohookean_residual_p2_500k.md",
+                                    ["common.cuh", "layout.h", "launch.cuh", "vec_forms.cuh", "log_f64.cuh",
+                                     "log_table.h"]),
 }
 
 
@@ -462,7 +466,8 @@ def run_vector(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         roof = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_kind": "derived: FP32 lanes x clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    full = E == VECTOR_WORKLOADS[args.workload][2]
+    roof["traffic"] = profiled_traffic(args.workload) if full and not f32 else None
     roof["alg_bytes_per_launch"] = alg_bytes
     roof["bound_times_ms"] = {"hbm": t_hbm * 1e3, "fp32": t_f32 * 1e3, "fp64": t_f64 * 1e3}
     line = {
