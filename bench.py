@@ -88,10 +88,13 @@ def profiled_traffic(workload):
     return float(m.group(1))
 
 
+CLOCKS_LOG = None  # --clocks-log: path of an nvidia-smi log of the timed regions
+
+
 class ClockSampler:
     """SM clock and clock-event reasons sampled through NVML (libnvidia-ml,
-    read-only queries) by a background thread during the timed region, plus an
-    nvidia-smi log of the same quantities written beside the run."""
+    read-only queries) by a background thread during the timed region, plus,
+    with --clocks-log, an nvidia-smi log of the same quantities."""
 
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
@@ -133,8 +136,11 @@ class ClockSampler:
     def __enter__(self):
         import threading
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.log = open(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv"), "w")
+            if not CLOCKS_LOG:
+                raise OSError("no nvidia-smi log requested")
+            d = os.path.dirname(os.path.abspath(CLOCKS_LOG))
+            os.makedirs(d, exist_ok=True)
+            self.log = open(CLOCKS_LOG, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -264,7 +270,10 @@ def main():
     ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_1604_05872_gb300", "data", "tuning_gb300.json"),
                     help="tuning JSON (records + MLP) for the stream workload ('' for the flop-count choice only)")
     ap.add_argument("--out-f32", action="store_true", help="FP32 output (element matrices stored as float)")
+    ap.add_argument("--clocks-log", default="", help="also log nvidia-smi clocks of the timed regions to this CSV")
     args = ap.parse_args()
+    global CLOCKS_LOG
+    CLOCKS_LOG = args.clocks_log or None
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))

@@ -44,7 +44,7 @@ def candidates(form, p, precision=fea.PREC_FP32):
     return out
 
 
-HBM_GBS = 6753.8           # measured copy bandwidth of the GB300s
+HBM_GBS = 6753.8           # GB300 copy bandwidth, STREAM-style measurement (a fixed feature scale)
 FP32_TFLOPS = 80.5         # 152 SMs x 128 lanes x 2 x 2.07 GHz
 FP64_TFLOPS = 1.26         # 152 SMs x 2 lanes x 2 x 2.07 GHz
 
