@@ -167,19 +167,20 @@ int fea_log_f64(const double* x, double* y, int64_t n, void* stream);
  * fea_csr_pattern (HOST arrays): the CSR sparsity pattern of a mesh whose
  * element e has global DOFs dofs[e][0..n) (int32, row-major [E][n]; vector
  * forms number DOF 3 a + c of a node a as the caller's global map says), with
- * sorted unique columns per row.  Two calls: first with col_idx = NULL to get
- * *nnz (row_ptr may be NULL too), then with row_ptr [nrows + 1] and col_idx
- * [*nnz] to fill them.  FEA_EINVAL for a DOF outside [0, nrows) or a col_idx
- * smaller than *nnz.
+ * sorted unique columns per row; upper = 1 keeps only columns >= row (the
+ * symmetric storage of a symmetric matrix), upper = 0 all.  Two calls: first
+ * with col_idx = NULL to get *nnz (row_ptr may be NULL too), then with row_ptr
+ * [nrows + 1] and col_idx [*nnz] to fill them.  FEA_EINVAL for a DOF outside
+ * [0, nrows), upper not 0 or 1, or a col_idx smaller than *nnz.
  *
- * fea_scatter_add_csr (DEVICE arrays, on `stream`): values[k] += elem[e][i][j]
- * for k the position of column dofs[e][j] in row dofs[e][i]; elem is [E][n][n]
- * double (elem_f32 = 0) or float (1), as fea_assemble writes it; values is
- * [nnz] double and is accumulated into (zero it first for a fresh matrix).
- * FP64 atomics: the sum order, and so the last bits, vary between runs.  A DOF,
- * row segment or column outside the pattern is skipped and makes the next
- * fea_sync return FEA_EINVAL. */
-int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nrows, int64_t* row_ptr,
+ * fea_scatter_add_csr (DEVICE arrays, on `stream`; full patterns): values[k]
+ * += elem[e][i][j] for k the position of column dofs[e][j] in row dofs[e][i];
+ * elem is [E][n][n] double (elem_f32 = 0) or float (1), as fea_assemble writes
+ * it; values is [nnz] double and is accumulated into (zero it first for a
+ * fresh matrix).  FP64 atomics: the sum order, and so the last bits, vary
+ * between runs.  A DOF, row segment or column outside the pattern is skipped
+ * and makes the next fea_sync return FEA_EINVAL. */
+int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nrows, int upper, int64_t* row_ptr,
                     int32_t* col_idx, int64_t* nnz);
 int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const void* elem, int elem_f32,
                         int64_t nrows, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz,
@@ -189,12 +190,15 @@ int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const void* elem,
  * fea_csr_scatter_map writes once, for every (e, i, j), the CSR position of
  * column dofs[e][j] in row dofs[e][i] into map [E][n][n] (device; int32 when
  * map_i64 = 0, which needs nnz < 2^31, else FEA_EINVAL; int64 when map_i64 = 1;
- * -1 and FEA_EINVAL at the next fea_sync where the pattern has no entry);
+ * -1 and FEA_EINVAL at the next fea_sync where the pattern has no entry; with
+ * upper = 1, for a pattern built with upper = 1, -2 for the entries below the
+ * diagonal, which are not stored and raise no error);
  * fea_scatter_add_csr_mapped then does values[map[e][i][j]] += elem[e][i][j]
- * with coalesced reads and no search (map_i64 as the map was written; a
- * position outside [0, nnz) is skipped and flagged like a missing entry). */
+ * with coalesced reads and no search (map_i64 as the map was written; -2
+ * entries are passed over; any other position outside [0, nnz) is skipped and
+ * flagged like a missing entry). */
 int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
-                        const int32_t* col_idx, int64_t nnz, void* map, int map_i64, void* stream);
+                        const int32_t* col_idx, int64_t nnz, int upper, void* map, int map_i64, void* stream);
 int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, const void* elem, int elem_f32,
                                int64_t nnz, double* values, void* stream);
 
@@ -203,7 +207,8 @@ int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, c
  * values at its position instead of storing the matrix: values[map[e][i][j]]
  * += A_e[i][j] (DEVICE arrays, on `stream`; coords and coeffs as for
  * fea_assemble; map [E][n][n] from fea_csr_scatter_map, int32 when map_i64 = 0
- * (nnz < 2^31) or int64; values [nnz] double, accumulated into).  FP32
+ * (nnz < 2^31) or int64; values [nnz] double, accumulated into; a map of an
+ * upper-triangle pattern assembles the symmetric storage).  FP32
  * contraction, FP64 atomics (the last bits of the sums vary between runs).
  * FEA_EINVAL for other forms and degrees (use fea_assemble, then
  * fea_scatter_add_csr_mapped); a position outside [0, nnz) is skipped and

@@ -83,9 +83,9 @@ def load(path=None):
     lib.fea_assemble_batch.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_assemble_batch_fused.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_assemble_vector.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
-    lib.fea_csr_pattern.argtypes = [i64, i, vp, i64, vp, vp, P(i64)]
+    lib.fea_csr_pattern.argtypes = [i64, i, vp, i64, i, vp, vp, P(i64)]
     lib.fea_scatter_add_csr.argtypes = [i64, i, vp, vp, i, i64, vp, vp, i64, vp, vp]
-    lib.fea_csr_scatter_map.argtypes = [i64, i, vp, i64, vp, vp, i64, vp, i, vp]
+    lib.fea_csr_scatter_map.argtypes = [i64, i, vp, i64, vp, vp, i64, i, vp, i, vp]
     lib.fea_log_f64.argtypes = [vp, vp, i64, vp]
     lib.fea_assemble_csr.argtypes = [i, i, i64, vp, vp, vp, i, i64, vp, vp]
     lib.fea_scatter_add_csr_mapped.argtypes = [i64, i, vp, i, vp, i, i64, vp, vp]
@@ -208,18 +208,19 @@ def assemble_vector(form, degree, coords, coeffs, out=None, precision=PREC_FP32,
     return out
 
 
-def csr_pattern(dofs, nrows):
+def csr_pattern(dofs, nrows, upper=False):
     """CSR pattern (row_ptr int64 [nrows + 1], col_idx int32 [nnz]) of the element-to-DOF map
-    `dofs` (host int32 array [E, n]); fea_csr_pattern, built on the host."""
+    `dofs` (host int32 array [E, n]); upper=True keeps columns >= row only (symmetric storage);
+    fea_csr_pattern, built on the host."""
     import numpy as np
     d = np.ascontiguousarray(dofs, dtype=np.int32)
     E, n = d.shape
     nnz = ctypes.c_int64(0)
-    _check(load().fea_csr_pattern(E, n, d.ctypes.data, nrows, None, None, ctypes.byref(nnz)))
+    _check(load().fea_csr_pattern(E, n, d.ctypes.data, nrows, int(bool(upper)), None, None, ctypes.byref(nnz)))
     row_ptr = np.empty(nrows + 1, dtype=np.int64)
     col_idx = np.empty(max(1, nnz.value), dtype=np.int32)
-    _check(load().fea_csr_pattern(E, n, d.ctypes.data, nrows, row_ptr.ctypes.data, col_idx.ctypes.data,
-                                  ctypes.byref(nnz)))
+    _check(load().fea_csr_pattern(E, n, d.ctypes.data, nrows, int(bool(upper)), row_ptr.ctypes.data,
+                                  col_idx.ctypes.data, ctypes.byref(nnz)))
     return row_ptr, col_idx[:nnz.value]
 
 
@@ -235,9 +236,10 @@ def scatter_add_csr(dofs, elem, row_ptr, col_idx, values, stream=None):
     return values
 
 
-def csr_scatter_map(dofs, row_ptr, col_idx, stream=None, index_dtype=None):
+def csr_scatter_map(dofs, row_ptr, col_idx, stream=None, index_dtype=None, upper=False):
     """CSR position of every (element, i, j) [E, n, n] (device); fea_csr_scatter_map.  int32
-    when the pattern has fewer than 2^31 entries (index_dtype=None), else int64."""
+    when the pattern has fewer than 2^31 entries (index_dtype=None), else int64; upper=True for a
+    pattern of the upper triangle (entries below the diagonal map to -2, not stored)."""
     import torch
     E, n = dofs.shape
     nnz = col_idx.shape[0]
@@ -245,7 +247,8 @@ def csr_scatter_map(dofs, row_ptr, col_idx, stream=None, index_dtype=None):
         index_dtype = torch.int32 if nnz < 2 ** 31 else torch.int64
     m = torch.empty((E, n, n), dtype=index_dtype, device=dofs.device)
     _check(load().fea_csr_scatter_map(E, n, _ptr(dofs), row_ptr.shape[0] - 1, _ptr(row_ptr), _ptr(col_idx),
-                                      nnz, _ptr(m), int(index_dtype == torch.int64), _stream_ptr(stream)))
+                                      nnz, int(bool(upper)), _ptr(m), int(index_dtype == torch.int64),
+                                      _stream_ptr(stream)))
     return m
 
 

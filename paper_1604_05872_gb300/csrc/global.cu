@@ -3,6 +3,10 @@
 // pattern of a mesh's element-to-DOF map, built on the host, and the GPU
 // scatter-add of element matrices into the CSR values.
 //
+// Symmetric storage: with `upper` set, the pattern holds the upper triangle
+// (column >= row) only; the position map marks the lower entries of an element
+// matrix with kSkipPos, which the scatters pass over without an error.
+//
 // Scatter: one thread per (element, local row i); the row's CSR segment is the
 // same for every local column j, each column is found by binary search in the
 // sorted segment and added with an FP64 atomic.  A column missing from the
@@ -20,6 +24,8 @@
 #include "common.cuh"
 
 namespace fea {
+
+constexpr int64_t kSkipPos = -2;  // map entry of a lower-triangle entry under symmetric storage
 
 template <typename TE>
 __global__ void __launch_bounds__(256) scatter_csr_kernel(int64_t E, int n, const int32_t* __restrict__ dofs,
@@ -64,7 +70,7 @@ template <typename TM>
 __global__ void __launch_bounds__(256) scatter_map_kernel(int64_t E, int n, const int32_t* __restrict__ dofs,
                                                           int64_t nrows, const int64_t* __restrict__ row_ptr,
                                                           const int32_t* __restrict__ col_idx, int64_t nnz,
-                                                          TM* map, unsigned* err) {
+                                                          int upper, TM* map, unsigned* err) {
   const int64_t rows = E * n;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < rows; w += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = w / n;
@@ -80,7 +86,9 @@ __global__ void __launch_bounds__(256) scatter_map_kernel(int64_t E, int n, cons
     const bool seg_ok = row_ok && lo0 >= 0 && hi0 >= lo0 && hi0 <= nnz;
     for (int j = 0; j < n; ++j) {
       int64_t pos = -1;
-      if (seg_ok) {
+      if (seg_ok && upper && __ldg(de + j) < r) {
+        pos = kSkipPos;
+      } else if (seg_ok) {
         const int32_t c = __ldg(de + j);
         int64_t lo = lo0, hi = hi0;
         while (lo < hi) {
@@ -90,7 +98,7 @@ __global__ void __launch_bounds__(256) scatter_map_kernel(int64_t E, int n, cons
         }
         if (lo < hi0 && __ldg(col_idx + lo) == c) pos = lo;
       }
-      if (pos < 0) flag_error(err, ERR_PATTERN);
+      if (pos == -1) flag_error(err, ERR_PATTERN);
       m[j] = (TM)pos;
     }
   }
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(256) scatter_mapped_kernel(int64_t total, cons
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pos = __ldg(map + k);
     if (pos >= 0 && pos < nnz) atomicAdd(values + pos, (double)__ldg(elem + k));
-    else flag_error(err, ERR_PATTERN);
+    else if (pos != kSkipPos) flag_error(err, ERR_PATTERN);
   }
 }
 
@@ -147,9 +155,10 @@ int scatter_impl(int64_t E, int n, const int32_t* dofs, const void* elem, int el
 constexpr int64_t kMaxMap32 = 2147483647;  // largest position an int32 map holds
 
 int scatter_map_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
-                     const int32_t* col_idx, int64_t nnz, void* map, int map_i64, void* stream) {
+                     const int32_t* col_idx, int64_t nnz, int upper, void* map, int map_i64, void* stream) {
   if (E < 0 || n < 1 || nrows < 0 || nnz < 0) return set_error(FEA_EINVAL, "negative size or empty local dimension");
   if (map_i64 != 0 && map_i64 != 1) return set_error(FEA_EINVAL, "map_i64 must be 0 or 1");
+  if (upper != 0 && upper != 1) return set_error(FEA_EINVAL, "upper must be 0 or 1");
   if (!map_i64 && nnz > kMaxMap32) return set_error(FEA_EINVAL, "nnz >= 2^31 needs an int64 map");
   if (E == 0) return FEA_OK;
   DevState* st = nullptr;
@@ -164,10 +173,10 @@ int scatter_map_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, const
   cudaStream_t s = (cudaStream_t)stream;
   unsigned* err = device_error_word(st);
   if (map_i64)
-    scatter_map_kernel<int64_t><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz,
+    scatter_map_kernel<int64_t><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz, upper,
                                                                static_cast<int64_t*>(map), err);
   else
-    scatter_map_kernel<int32_t><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz,
+    scatter_map_kernel<int32_t><<<(unsigned)grid, 256, 0, s>>>(E, n, dofs, nrows, row_ptr, col_idx, nnz, upper,
                                                                static_cast<int32_t*>(map), err);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
@@ -209,15 +218,17 @@ int scatter_mapped_impl(int64_t E, int n, const void* map, int map_i64, const vo
 }
 
 // CSR pattern of sum_K (dofs_K x dofs_K): sorted unique columns per row.
-int csr_pattern_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, int64_t* row_ptr, int32_t* col_idx,
-                     int64_t* nnz) {
+int csr_pattern_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, int upper, int64_t* row_ptr,
+                     int32_t* col_idx, int64_t* nnz) {
   if (E < 0 || n < 1 || nrows < 0 || !nnz || (E > 0 && !dofs)) return set_error(FEA_EINVAL, "bad pattern arguments");
+  if (upper != 0 && upper != 1) return set_error(FEA_EINVAL, "upper must be 0 or 1");
   std::vector<std::vector<int32_t>> cols((size_t)nrows);
   for (int64_t e = 0; e < E; ++e) {
     const int32_t* d = dofs + e * n;
     for (int i = 0; i < n; ++i) {
       if (d[i] < 0 || d[i] >= nrows) return set_error(FEA_EINVAL, "a DOF index is outside [0, nrows)");
-      for (int j = 0; j < n; ++j) cols[(size_t)d[i]].push_back(d[j]);
+      for (int j = 0; j < n; ++j)
+        if (!upper || d[j] >= d[i]) cols[(size_t)d[i]].push_back(d[j]);
     }
   }
   int64_t total = 0;
@@ -248,14 +259,15 @@ extern "C" int fea_scatter_add_csr(int64_t E, int n, const int32_t* dofs, const 
   return fea::scatter_impl(E, n, dofs, elem, elem_f32, nrows, row_ptr, col_idx, nnz, values, stream);
 }
 
-extern "C" int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nrows, int64_t* row_ptr,
+extern "C" int fea_csr_pattern(int64_t E, int n, const int32_t* dofs, int64_t nrows, int upper, int64_t* row_ptr,
                                int32_t* col_idx, int64_t* nnz) {
-  return fea::csr_pattern_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz);
+  return fea::csr_pattern_impl(E, n, dofs, nrows, upper, row_ptr, col_idx, nnz);
 }
 
 extern "C" int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_t nrows, const int64_t* row_ptr,
-                                   const int32_t* col_idx, int64_t nnz, void* map, int map_i64, void* stream) {
-  return fea::scatter_map_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz, map, map_i64, stream);
+                                   const int32_t* col_idx, int64_t nnz, int upper, void* map, int map_i64,
+                                   void* stream) {
+  return fea::scatter_map_impl(E, n, dofs, nrows, row_ptr, col_idx, nnz, upper, map, map_i64, stream);
 }
 
 extern "C" int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, const void* elem,

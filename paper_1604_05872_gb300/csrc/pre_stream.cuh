@@ -193,10 +193,11 @@ __device__ __forceinline__ void scatter_pair(const ScatterArgs& sc, int64_t k, d
     m0 = m.x;
     m1 = m.y;
   }
+  // -2: a lower-triangle entry under symmetric storage, not stored
   if (m0 >= 0 && m0 < sc.nnz) atomicAdd(sc.values + m0, v0);
-  else flag_error(err, ERR_PATTERN);
+  else if (m0 != -2) flag_error(err, ERR_PATTERN);
   if (m1 >= 0 && m1 < sc.nnz) atomicAdd(sc.values + m1, v1);
-  else flag_error(err, ERR_PATTERN);
+  else if (m1 != -2) flag_error(err, ERR_PATTERN);
 }
 
 // MAPW 0: store the element matrices; 4 or 8: add them into the CSR values.

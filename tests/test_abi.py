@@ -88,9 +88,10 @@ def test_shared_memory_budget_is_constraint_two(lib):
 def test_scatter_argument_checks_without_gpu(lib):
     # argument errors are answered before any device access
     nul = ctypes.c_void_p(0)
-    assert lib.fea_csr_scatter_map(10, 4, nul, 5, nul, nul, 2 ** 31, nul, 0, nul) == fea.EINVAL
+    assert lib.fea_csr_scatter_map(10, 4, nul, 5, nul, nul, 2 ** 31, 0, nul, 0, nul) == fea.EINVAL
     assert "int64 map" in lib.fea_last_error().decode()
-    assert lib.fea_csr_scatter_map(10, 4, nul, 5, nul, nul, 100, nul, 2, nul) == fea.EINVAL
+    assert lib.fea_csr_scatter_map(10, 4, nul, 5, nul, nul, 100, 0, nul, 2, nul) == fea.EINVAL
+    assert lib.fea_csr_scatter_map(10, 4, nul, 5, nul, nul, 100, 3, nul, 0, nul) == fea.EINVAL
     assert lib.fea_scatter_add_csr_mapped(10, 4, nul, 3, nul, 0, 100, nul, nul) == fea.EINVAL
     assert lib.fea_scatter_add_csr_mapped(-1, 4, nul, 0, nul, 0, 100, nul, nul) == fea.EINVAL
 

@@ -30,6 +30,22 @@ def test_csr_pattern_matches_library_sparse_sum(p):
 
 
 @pytest.mark.parametrize("p", [1, 2])
+def test_upper_pattern_is_the_upper_triangle(p):
+    """Symmetric storage: the pattern with upper=True is the upper triangle (diagonal included) of
+    the full pattern, row by row, and holds (nnz + nrows) / 2 entries."""
+    import paper_1604_05872_gb300 as fea
+    coords, dofs, nd = inputs.box_mesh(3, p, jitter=0.2)
+    rp, ci = fea.csr_pattern(dofs, nd)
+    ur, uc = fea.csr_pattern(dofs, nd, upper=True)
+    indptr, indices, _ = global_ref.assemble_csr(dofs, np.ones((dofs.shape[0],) + (dofs.shape[1],) * 2), nd, upper=True)
+    assert np.array_equal(ur, indptr) and np.array_equal(uc, indices)
+    assert 2 * uc.shape[0] == ci.shape[0] + nd
+    for r in range(nd):
+        row = ci[rp[r]:rp[r + 1]]
+        assert np.array_equal(uc[ur[r]:ur[r + 1]], row[row >= r])
+
+
+@pytest.mark.parametrize("p", [1, 2])
 def test_reference_global_matrices_on_the_unit_cube(orc, p):
     """Mass: the entries sum to the volume (1).  Laplacian (Helmholtz with
     f = 0): zero row sums, and u^T K u = int |grad u|^2 = 1 for u = x, exact
@@ -198,3 +214,41 @@ def test_gpu_one_pass_rejects_and_flags(fea):
     m = fea.assemble(0, 1, c).cpu().numpy()
     assert abs(m.sum() - 1.0) < 1e-6
     assert abs(float(vals.sum()) - (m.sum() - m[5, 1, 2] - m[9, 0, 0])) < 1e-13
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form,p", [(0, 1), (1, 2)])
+def test_gpu_symmetric_storage(fea, orc, form, p):
+    """Upper-triangle pattern and map: the one-pass and the mapped scatter both give the upper
+    triangle of the full global matrix; entries below the diagonal are passed over without an error."""
+    import torch
+    rng = np.random.default_rng(17)
+    coords, dofs, nd = inputs.box_mesh(6, p, jitter=0.1)
+    E = coords.shape[0]
+    coeffs = None if form == 0 else inputs.random_coeffs(form, p, E, rng)
+    c = torch.from_numpy(coords).cuda()
+    f = None if coeffs is None else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
+    dd = torch.from_numpy(dofs).cuda()
+    ur, uc = fea.csr_pattern(dofs, nd, upper=True)
+    umap = fea.csr_scatter_map(dd, torch.from_numpy(ur).cuda(), torch.from_numpy(uc).cuda(), upper=True)
+    fea.sync()  # no entry is missing: the lower ones are marked, not flagged
+    assert int((umap == -2).sum()) == int((dofs[:, None, :] < dofs[:, :, None]).sum())
+    assert int((umap == -1).sum()) == 0
+    one = fea.assemble_csr(form, p, c, f, umap, torch.zeros(uc.shape[0], dtype=torch.float64, device="cuda"))
+    two = fea.scatter_add_csr_mapped(umap, fea.assemble(form, p, c, f), torch.zeros_like(one))
+    fea.sync()
+    full_r, full_c = fea.csr_pattern(dofs, nd)
+    fmap = fea.csr_scatter_map(dd, torch.from_numpy(full_r).cuda(), torch.from_numpy(full_c).cuda())
+    full = fea.assemble_csr(form, p, c, f, fmap, torch.zeros(full_c.shape[0], dtype=torch.float64, device="cuda"))
+    fea.sync()
+    import scipy.sparse as sp
+    A = sp.csr_matrix((full.cpu().numpy(), full_c, full_r), shape=(nd, nd))
+    U = sp.triu(A, k=0, format="csr")
+    U.sort_indices()
+    assert np.array_equal(U.indptr, ur) and np.array_equal(U.indices, uc)
+    scale = float(np.abs(U.data).max())
+    assert np.abs(one.cpu().numpy() - U.data).max() <= 1e-12 * scale
+    assert np.abs(two.cpu().numpy() - U.data).max() <= 1e-12 * scale
+    # against the oracle's element matrices
+    _, _, ref = global_ref.assemble_csr(dofs, orc.assemble(form, p, coords, coeffs), nd, upper=True)
+    assert np.linalg.norm(one.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
