@@ -96,8 +96,18 @@ struct SeVecTile {
     return a > b ? a : b;
   }
 
+  // The tile the thread layout is built for (TEMAX) runs with the tile size and
+  // the point count as compile-time constants (shared-memory offsets and row
+  // strides fold into immediates); other tiles take the same code with runtime
+  // sizes.
   __device__ static void tile(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
-    const int TE = q.tile, Q = q.Q;
+    if (q.tile == TEMAX) tile_t<TEMAX>(q, e0, ne, sm, err);
+    else tile_t<0>(q, e0, ne, sm, err);
+  }
+
+  template <int TEC>
+  __device__ static void tile_t(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
+    const int TE = TEC ? TEC : q.tile, Q = q.Q;
     double* xs = reinterpret_cast<double*>(sm);
     double* cs = reinterpret_cast<double*>(sm + off_c(TE));
     T* ct = reinterpret_cast<T*>(sm + off_ct(TE));

@@ -58,6 +58,21 @@ def test_flop_reduced_variants_match_oracle(fea, orc, form, p, prec):
         assert err.max() <= TOL[prec], (form, p, variant, prec, err.max())
 
 
+@pytest.mark.parametrize("form,p", [(2, 1), (2, 2), (3, 1), (3, 2), (3, 3)])
+def test_vector_se_smaller_tile(fea, orc, form, p):
+    """The sharing-elimination tile kernel at a tile below the one its thread layout is built for
+    (runtime tile sizes instead of compile-time ones), several tiles and a ragged tail."""
+    t = fea.plan(form, p, variant=1)["tile"]
+    small = max(1, t - 1) if t > 1 else 1
+    E = 3 * small + 1
+    coords, coeffs = inputs.workload(form, p, E, seed=1500 + 10 * form + p)
+    c, f = to_dev(coords, coeffs, form, p)
+    out = fea.assemble(form, p, c, f, variant=1, tile=small)
+    fea.sync()
+    err = orc.rel_frobenius(out.cpu().numpy(), oracle_ref(orc, form, p, coords, coeffs))
+    assert err.max() <= TOL[1], (form, p, small, err.max())
+
+
 @pytest.mark.parametrize("p", DEGREES)
 @pytest.mark.parametrize("form", FORMS)
 def test_plain_fp64_kernel_matches_oracle(fea, orc, form, p):
