@@ -82,19 +82,34 @@ POISSON_B = ("e,i,k: t0[k] = z0[e]*a[i,k] + z2[e]*b[i,k]; e,i,k: t1[k] = z1[e]*a
              "e,i,j,k: A[e,j,k] += t0[k]*t2[j] + t1[k]*t3[j]")
 
 
+def paper_values():
+    """Values the paper prints (tests/golden/paper_values.json, each with its citation)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.json")) as f:
+        return json.load(f)
+
+
 @pytest.mark.parametrize("E,I,J,K", [(1, 3, 3, 3), (2, 4, 3, 5), (1, 6, 6, 6)])
 def test_poisson_counts(E, I, J, K):
+    g = paper_values()["poisson_2d"]
     ext = {"e": E, "i": I, "j": J, "k": K}
-    assert check_tally("e,i,j,k: A[e,j,k] += " + POISSON, ext) == E * I * J * K * 18
+    assert check_tally("e,i,j,k: A[e,j,k] += " + POISSON, ext) == E * I * J * K * g["naive_ops_per_eijk"]
     # the listing of Figure "poisson" (b): 6 per k, 9 per j (W_i det counted once), 4 per (j, k)
-    assert check_tally(POISSON_B, ext) == E * I * (6 * K + 9 * J + 4 * J * K)
+    c = g["se_coefficients_of_the_listing"]
+    assert check_tally(POISSON_B, ext) == E * I * (c["K"] * K + c["J"] * J + c["JK"] * J * K)
+    # the caption's printed count, with its J and K labels swapped back, is the same polynomial
+    pr = g["se_coefficients_as_printed"]
+    assert (pr["J"], pr["K"], pr["JK"]) == (c["K"], c["J"], c["JK"])
+    if J == K:  # where the example lives, the printed count holds as printed
+        assert check_tally(POISSON_B, ext) == E * I * (pr["J"] * J + pr["K"] * K + pr["JK"] * J * K)
 
 
 @pytest.mark.parametrize("E,I,J,K", [(1, 3, 3, 3), (2, 4, 3, 5), (1, 2, 6, 4)])
 def test_poisson_sharing_elimination(E, I, J, K):
     ext = {"e": E, "i": I, "j": J, "k": K}
     prog, ops, cover = fea.sharing_elimination("A[e,j,k]", POISSON, ["e", "i", "j", "k"], ext)
-    assert cover == 2  # two products per innermost iteration (Figure "poisson" (b))
+    assert cover == paper_values()["poisson_2d"]["vertex_cover"]  # two products per innermost iteration
     assert ops == check_tally(prog, ext)
     # generalized code motion hoists W_i det to the i loop (1 per i) and the
     # coefficient products run over the smaller linear loop
@@ -126,7 +141,8 @@ def test_reduction_pre_evaluation_counts():
 
 def test_increase_factor():
     # Section 4.2: iota = 3 for n = 3, k = 1 and iota = 6 for k = 2
-    assert fea.increase_factor(3, 1) == 3 and fea.increase_factor(3, 2) == 6
+    for ex in paper_values()["increase_factor"]["examples"]:
+        assert fea.increase_factor(ex["n"], ex["k"]) == ex["iota"]
     assert fea.increase_factor(10, 1) == 10 and fea.increase_factor(4, 0) == 1
     from math import comb
     for n in range(1, 9):
@@ -163,6 +179,15 @@ def test_theta_pre_structure():
     # f-mass rho = 1, iota = n = 10; tables = 6 + 10 = the kernel's reference terms
     th = fea.theta(1, 2)
     assert th[0][2] == 6 * 100 and th[1][2] == 10 * 100
+    # the paper's rho: 1 for a mass monomial (Helmholtz's f-mass term above: one table per coefficient
+    # DOF), 3 for the 2-D Poisson geometry tensor (d (d + 1) / 2 with d = 2; 6 for d = 3 here)
+    rho = paper_values()["rho"]
+    for p in (1, 2, 3):
+        nn = fea.local_dim(0, p) ** 2
+        assert fea.theta(0, p)[0][2] == rho["mass_monomial"] * nn  # mass: one table
+    # stiffness: one table per entry of the symmetric d x d geometry tensor, d (d + 1) / 2:
+    # the paper's 3 in two dimensions, 6 here in three
+    assert rho["poisson_2d"] == 2 * 3 // 2 and th[0][2] == (3 * 4 // 2) * 100
     assert fea.plan(1, 2)["ref_terms"] == 16
     # iota >= Q makes pre-evaluation unprofitable: elasticity P1 (iota = 4, Q = 1)
     se, pre, _ = fea.theta(2, 1)[0]
