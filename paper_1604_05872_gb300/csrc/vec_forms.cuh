@@ -91,6 +91,7 @@ struct ResVecTile {
   static constexpr int TE = P <= 2 ? 32 : P == 3 ? 16 : 8;
   static constexpr int GEO = 12;                 // Jinv[9], |det|
   static constexpr int TW = 12;                  // T_q[3][3] padded
+  static constexpr int MINB = sizeof(T) == 4 && P <= 2 ? 3 : 1;  // resident CTAs per SM
 
   FEA_HD static int max_tile() { return TE; }
   FEA_HD static int pref_tile() { return TE; }
@@ -100,8 +101,17 @@ struct ResVecTile {
   FEA_HD static size_t off_t(int te) { return off_geo(te) + round_up_sz((size_t)te * GEO * sizeof(T), 16); }
   FEA_HD static size_t smem(int te, int Q) { return off_t(te) + round_up_sz((size_t)te * Q * TW * sizeof(T), 16); }
 
+  // The default tile with the form's own rule, (P + 1)^3 points, runs with both as
+  // compile-time constants (index arithmetic folds); other tiles and rules at run time.
+  static constexpr int QDEF = (P + 1) * (P + 1) * (P + 1);
   __device__ static void tile(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
-    const int te = q.tile, Q = q.Q;
+    if (q.tile == TE && q.Q == QDEF) tile_t<TE, QDEF>(q, e0, ne, sm, err);
+    else tile_t<0, 0>(q, e0, ne, sm, err);
+  }
+
+  template <int TEC, int QC>
+  __device__ static void tile_t(const Req& q, int64_t e0, int ne, char* sm, unsigned* err) {
+    const int te = TEC ? TEC : q.tile, Q = QC ? QC : q.Q;
     double* xs = reinterpret_cast<double*>(sm);
     double* cs = reinterpret_cast<double*>(sm + off_c(te));
     T* ct = reinterpret_cast<T*>(sm + off_ct(te));
@@ -123,10 +133,17 @@ struct ResVecTile {
       const bool bad = !(fabs(det) > 0.0) || !isfinite(det);
       if (bad) flag_error(err, ERR_DEGENERATE);
       T* g = geo + GEO * tid;
-      const double inv = 1.0 / det;
+      if constexpr (sizeof(T) == 4) {  // the division is a well-conditioned scaling after rounding
+        const float df = d2f(det), inv = 1.0f / df;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) g[k] = bad ? nan : from_double<T>(adj[k] * inv);
-      g[9] = bad ? nan : from_double<T>(fabs(det));
+        for (int k = 0; k < 9; ++k) g[k] = bad ? nan : d2f(adj[k]) * inv;
+        g[9] = bad ? nan : fabsf(df);
+      } else {
+        const double inv = 1.0 / det;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) g[k] = bad ? nan : adj[k] * inv;
+        g[9] = bad ? nan : fabs(det);
+      }
     }
     for (int k = tid; k < ne * CLEN; k += NT) ct[k] = from_double<T>(cs[k]);
     __syncthreads();
