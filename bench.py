@@ -461,7 +461,7 @@ def run_vector(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     if form == 1:
         flops, f64 = 2 * ns * ns + ns, 20
     else:
-        flops, f64 = Q * (2 * 9 * ns + 2 * 27 + 2 * 27 + 2 * 27 + 18 * ns), 50 + NEO_POINT_FP64 * Q
+        flops, f64 = Q * (2 * 9 * ns + 2 * 27 + 2 * 27 + 2 * 27 + 18 * ns), 30 + NEO_POINT_FP64 * Q
     hbm, peak_kind = peaks()
     alg_bytes, fl, f64t = E * bytes_elem, E * flops, E * f64
     t_hbm, t_f32, t_f64 = alg_bytes / (hbm * 1e9), fl / (FP32_PEAK_TFLOPS * 1e12), f64t / (FP64_PEAK_TINSTR * 1e12)
