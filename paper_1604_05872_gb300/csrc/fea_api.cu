@@ -203,6 +203,7 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
   pl->tile = TE;
   pl->Q = Q;
   pl->smem = smem;
+  pl->shrink_small = o.tile == 0 && !batch && k->pref_tile == 0;
   return FEA_OK;
 }
 
@@ -232,6 +233,17 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
   TableEntry* te = nullptr;
   int rc = get_tables(st, form, p, pl.prec, &te);
   if (rc) return rc;
+  int tile = pl.tile;
+  size_t smem_bytes = pl.smem;
+  if (pl.shrink_small && st->sms > 0) {
+    // fewer elements than one tile per SM: whole-warp tiles of about E / SMs elements
+    const int64_t per_sm = (E + st->sms - 1) / st->sms;
+    const int64_t t = std::max<int64_t>(32, (per_sm + 31) / 32 * 32);
+    if (t < tile) {
+      tile = (int)t;
+      smem_bytes = pl.k->smem(tile, pl.Q);
+    }
+  }
   Req q;
   q.coords = coords;
   q.coeffs = coeffs;
@@ -241,11 +253,11 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
   q.form = form;
   q.p = p;
   q.Q = pl.Q;
-  q.tile = pl.tile;
+  q.tile = tile;
   q.out_f32 = out_f32;
   q.kind = 0;
   q.tile0 = 0;
-  const int64_t ntiles = (E + pl.tile - 1) / pl.tile;
+  const int64_t ntiles = (E + tile - 1) / tile;
   int per_sm = 0;
   {
     // the opt-in shared-memory ceiling is raised once per kernel and device (it only
@@ -253,15 +265,15 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
     static std::mutex mu;
     static std::map<std::tuple<const void*, size_t, int>, int> occ;
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_tuple(pl.k->fn, pl.smem, st->dev);
+    auto key = std::make_tuple(pl.k->fn, smem_bytes, st->dev);
     auto it = occ.find(key);
     if (it == occ.end()) {
       cudaFuncAttributes fa;
       CUDA_TRY(cudaFuncGetAttributes(&fa, pl.k->fn));
       const int ceiling = (int)st->smem_optin - (int)fa.sharedSizeBytes;  // minus the kernel's static shared memory
-      if ((int)pl.smem > ceiling) return fail(FEA_EINVAL, "tile does not fit the device's shared memory");
+      if ((int)smem_bytes > ceiling) return fail(FEA_EINVAL, "tile does not fit the device's shared memory");
       CUDA_TRY(cudaFuncSetAttribute(pl.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ceiling));
-      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, NT, pl.smem));
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, NT, smem_bytes));
       occ[key] = per_sm;
     } else {
       per_sm = it->second;
@@ -270,7 +282,7 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
   if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with this tile");
   L->fn = pl.k->fn;
   L->grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
-  L->smem = pl.smem;
+  L->smem = smem_bytes;
   L->q = q;
   L->err = st->err;
   return FEA_OK;
@@ -346,25 +358,25 @@ int assemble_csr_impl(int form, int degree, int64_t E, const double* coords, con
     static std::mutex mu;
     static std::map<std::tuple<const void*, size_t, int>, int> occ;
     std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_tuple(fn, pl.smem, st->dev);
+    auto key = std::make_tuple(fn, L.smem, st->dev);
     auto it = occ.find(key);
     if (it == occ.end()) {
       cudaFuncAttributes fa;
       CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
       CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)st->smem_optin - (int)fa.sharedSizeBytes));
-      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, pl.smem));
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, L.smem));
       occ[key] = per_sm;
     } else {
       per_sm = it->second;
     }
   }
   if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with this tile");
-  const int64_t ntiles = (E + pl.tile - 1) / pl.tile;
+  const int64_t ntiles = (E + L.q.tile - 1) / L.q.tile;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
   ScatterArgs sc{map, nnz, values};
   void* args[] = {&L.q, &sc, &L.err};
-  CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, pl.smem, (cudaStream_t)stream));
+  CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, L.smem, (cudaStream_t)stream));
   return FEA_OK;
 }
 

@@ -13,6 +13,10 @@ struct Plan {
   const KernelInfo* k = nullptr;
   int variant = 0, prec = 1, tile = 0, Q = 0;
   size_t smem = 0;
+  // the tile came from the planner's rule for a kernel whose thread layout does
+  // not depend on it: a launch with fewer elements than SMs x tile may use a
+  // smaller one, so that every SM gets work and a tile's latency chain shortens
+  bool shrink_small = false;
 };
 
 // A launch resolved on the host (kernel, persistent grid, shared memory, request).
