@@ -74,8 +74,9 @@ struct SeVecTile {
   static_assert(GROUPS >= 1, "one element group must fit the CTA");
   static constexpr int TEMAX = EF * GROUPS;
   static constexpr int NSP = NS | 1;                 // row slots per element (odd)
-  // points per barrier (measured best per degree; Neo-Hookean P2: its 27 points in three groups of nine)
-  static constexpr int QG = NEO && P == 2 ? 9 : P >= 3 ? 16 : 4;
+  // points per barrier (measured best per degree; Neo-Hookean P2 and P4: their 27 and 125 points in
+  // groups of nine and 25, without padding)
+  static constexpr int QG = NEO && P == 2 ? 9 : NEO && P == 4 ? 25 : P >= 3 ? 16 : 4;
   static constexpr int GEO = 12;                     // Jinv[9], |det|, pad
   static constexpr int PW = NEO ? 20 : 4;            // per (e, q): [Fi[9], s mu F[9],] s alpha, s lam
   static constexpr int RW = NEO ? 2 : 1;             // 16-byte rows per (e, a): Y [, Z]
