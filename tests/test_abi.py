@@ -103,3 +103,11 @@ def test_one_pass_global_assembly_argument_checks_without_gpu(lib):
         assert lib.fea_assemble_csr(form, p, 10, nul, nul, nul, w, nnz, nul, nul) == fea.EINVAL, (form, p, nnz, w)
     lib.fea_assemble_csr(2, 1, 10, nul, nul, nul, 0, 100, nul, nul)
     assert "one-pass" in lib.fea_last_error().decode()
+
+
+def test_log_and_pattern_argument_checks_without_gpu(lib):
+    nul = ctypes.c_void_p(0)
+    assert lib.fea_log_f64(nul, nul, -1, nul) == fea.EINVAL
+    assert lib.fea_log_f64(nul, nul, 0, nul) == 0  # nothing to do
+    nnz = ctypes.c_int64(0)
+    assert lib.fea_csr_pattern(1, 4, nul, 10, 2, nul, nul, ctypes.byref(nnz)) == fea.EINVAL  # upper not 0/1
