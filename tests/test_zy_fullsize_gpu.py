@@ -113,3 +113,38 @@ def test_element_vector_workload_full_size(fea, orc, name, form, p, E):
         assert float(bal.max()) <= 1e-5
     del out, c, f
     torch.cuda.empty_cache()
+
+
+def test_global_assembly_full_size(fea, orc):
+    """The global assembly workload at its full size (Helmholtz P2 on the 55^3-cube mesh, 998 250
+    elements), in bench.py's launch configuration: the row sums of the assembled matrix are the
+    assembled load vector (the stiffness rows sum to zero, the f-mass rows to int f phi_i), checked
+    against the oracle's element load vectors summed at the global DOFs, to the FP32 contraction's
+    tolerance relative to each row's absolute sum; symmetric storage holds the upper triangle of the
+    full matrix."""
+    import torch
+    coords, dofs, nd = inputs.box_mesh(55, 2, jitter=0.1, seed=inputs.SEED)
+    E = coords.shape[0]
+    f = inputs.random_coeffs(1, 2, E, np.random.Generator(np.random.PCG64(inputs.SEED + 7)))
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd)
+    c = torch.from_numpy(coords).cuda()
+    fc = torch.from_numpy(inputs.coeff_array(1, 2, f)).cuda()
+    dd = torch.from_numpy(dofs).cuda()
+    smap = fea.csr_scatter_map(dd, torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col_idx).cuda())
+    vals = fea.assemble_csr(1, 2, c, fc, smap, torch.zeros(col_idx.shape[0], dtype=torch.float64, device="cuda"))
+    fea.sync()
+    v = vals.cpu().numpy()
+    assert np.isfinite(v).all()
+    rows = np.add.reduceat(v, row_ptr[:-1])
+    absrows = np.add.reduceat(np.abs(v), row_ptr[:-1])
+    b = orc.load_vector(2, coords, f)
+    ref = np.bincount(dofs.ravel(), weights=b.ravel(), minlength=nd)
+    assert np.all(np.abs(rows - ref) <= TOL * absrows)
+    # symmetric storage: the upper triangle of the same matrix
+    ur, uc = fea.csr_pattern(dofs, nd, upper=True)
+    umap = fea.csr_scatter_map(dd, torch.from_numpy(ur).cuda(), torch.from_numpy(uc).cuda(), upper=True)
+    uv = fea.assemble_csr(1, 2, c, fc, umap, torch.zeros(uc.shape[0], dtype=torch.float64, device="cuda"))
+    fea.sync()
+    r = np.repeat(np.arange(nd), np.diff(row_ptr))
+    keep = col_idx >= r
+    assert np.allclose(uv.cpu().numpy(), v[keep], rtol=0, atol=1e-12 * np.abs(v).max())
