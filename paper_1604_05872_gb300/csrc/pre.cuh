@@ -37,6 +37,7 @@ struct PreTile {
   static constexpr int S = NC == 1 ? NN / VJ : NS * NS;            // slots per element
   static constexpr int G = S >= NT ? 1 : NT / S;                   // element groups
   static constexpr int GEO = 12;                                   // adj[9], |det|, 1/|det|, pad
+  static constexpr int MINB = sizeof(T) == 4 && P == 4 ? 3 : 1;     // resident CTAs per SM
 
   FEA_HD static size_t off_c(int TE) { return round_up_sz((size_t)TE * 12 * 8, 16); }
   FEA_HD static size_t off_geo(int TE) { return off_c(TE) + round_up_sz((size_t)TE * CLEN * 8, 16); }
