@@ -86,6 +86,7 @@ __device__ __forceinline__ void pre_vec_block(const T* g, const T (&R)[36], T (&
 
 template <int P, typename T>
 struct PreVecTile {
+  static constexpr int MINB = sizeof(T) == 4 && P == 4 ? 3 : 1;  // resident CTAs per SM
   static constexpr int FORM = 2;
   static constexpr int NS = nbasis_c(P);
   static constexpr int N = 3 * NS;
