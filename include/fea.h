@@ -73,8 +73,15 @@ typedef enum {
  * i.e. det J * J^-1) and the Neo-Hookean det F, F^-1, ln det F are FP64 in
  * every mode. */
 typedef enum {
-  FEA_PREC_FP64 = 0,  /* everything FP64 (parity path, <= 1e-12 relative) */
-  FEA_PREC_FP32 = 1   /* FP32 contraction and pointwise work, FP64 geometry */
+  FEA_PREC_FP64 = 0,   /* everything FP64 (parity path, <= 1e-12 relative) */
+  FEA_PREC_FP32 = 1,   /* FP32 contraction and pointwise work, FP64 geometry */
+  FEA_PREC_BF16X2 = 2  /* split-BF16 tensor-core contraction where the contraction is dense and
+                        * compute-bound (the Neo-Hookean tangent at P2): both operands as
+                        * hi + lo BF16 pairs, all four products on tcgen05 tensor cores with
+                        * FP32 accumulation (<= 1e-5 relative); the per-point kinematics as
+                        * in FEA_PREC_FP32.  Every other (form, degree) runs the FP32
+                        * contraction in this mode (they are bound by HBM, not by the
+                        * contraction).  fea_assemble_batch accepts it; the fused batch does not. */
 } fea_precision;
 
 /* Loop-nest variant (Section 4, Figure "loopnest-opt"). */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libfea.so")
 MASS, HELMHOLTZ, ELASTICITY, NEOHOOKEAN = 0, 1, 2, 3
 FORMS = {"mass": MASS, "helmholtz": HELMHOLTZ, "elasticity": ELASTICITY, "neohookean": NEOHOOKEAN}
 OK, EINVAL, ENOMEM, ECUDA, EDEGENERATE, ETIMEOUT = 0, 1, 2, 3, 4, 5
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_BF16X2 = 0, 1, 2
 VARIANT_AUTO, VARIANT_NAIVE, VARIANT_SE, VARIANT_PRE = -1, 0, 1, 2
 VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
@@ -287,15 +287,15 @@ def scatter_add_csr_mapped(scatter_map, elem, values, stream=None):
     return values
 
 
-def assemble_batch(requests, out_f32=False, stream=None, fused=False):
+def assemble_batch(requests, out_f32=False, stream=None, fused=False, precision=PREC_FP32):
     """requests: list of (form, degree, coords, coeffs, out) device tensors, one CUDA graph launch
     (fea_assemble_batch: one persistent kernel per request; fused=True: fea_assemble_batch_fused,
-    one persistent kernel over a work list of all requests' tiles)."""
+    one persistent kernel over a work list of all requests' tiles, FP32 only)."""
     arr = (Request * len(requests))()
     for k, (form, degree, coords, coeffs, out) in enumerate(requests):
         arr[k] = Request(form, degree, coords.shape[0], coords.data_ptr(),
                          None if coeffs is None else coeffs.data_ptr(), out.data_ptr())
-    o = options(PREC_FP32, out_f32)
+    o = options(precision, out_f32)
     fn = load().fea_assemble_batch_fused if fused else load().fea_assemble_batch
     _check(fn(arr, len(requests), ctypes.byref(o), _stream_ptr(stream)))
 

@@ -245,7 +245,8 @@ int batch_fused_impl(const fea_request* reqs, int nreq, const fea_options* opt, 
 static bool same_launches(const std::vector<PreparedLaunch>& a, const std::vector<PreparedLaunch>& b) {
   if (a.size() != b.size()) return false;
   for (size_t i = 0; i < a.size(); ++i)
-    if (a[i].fn != b[i].fn || a[i].grid != b[i].grid || a[i].smem != b[i].smem || a[i].err != b[i].err ||
+    if (a[i].fn != b[i].fn || a[i].grid != b[i].grid || a[i].threads != b[i].threads || a[i].smem != b[i].smem ||
+        a[i].err != b[i].err ||
         std::memcmp(&a[i].q, &b[i].q, sizeof(Req)) != 0)
       return false;
   return true;
@@ -257,7 +258,8 @@ int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* 
   fea_options o;
   if (opt) o = *opt;
   else { o.precision = FEA_PREC_FP32; o.out_f32 = 0; o.variant = FEA_VARIANT_AUTO; o.tile = 0; o.smem_budget = 0; }
-  if (o.precision != FEA_PREC_FP32) return set_error(FEA_EINVAL, "the batched launch runs the FP32 contraction");
+  if (o.precision != FEA_PREC_FP32 && o.precision != FEA_PREC_BF16X2)
+    return set_error(FEA_EINVAL, "the batched launch runs the FP32 or split-BF16 contraction");
   DevState* st = nullptr;
   int rc = get_dev_state(&st);
   if (rc) return rc;
@@ -309,7 +311,7 @@ int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* 
         if (load[b] < load[k]) k = b;
       load[k] += work[i].first;
       void* args[] = {&L[i].q, &L[i].err};
-      e = cudaLaunchKernel(L[i].fn, dim3(L[i].grid), dim3(NT), args, L[i].smem, bs->br[k]);
+      e = cudaLaunchKernel(L[i].fn, dim3(L[i].grid), dim3(L[i].threads), args, L[i].smem, bs->br[k]);
     }
     for (int k = 1; k < kBranches && e == cudaSuccess; ++k) {
       e = cudaEventRecord(bs->ev[k], bs->br[k]);

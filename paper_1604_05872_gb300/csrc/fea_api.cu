@@ -20,6 +20,9 @@
 
 namespace fea {
 
+bool tc_table_words(int form, int p, std::vector<uint32_t>* words);
+const KernelInfo* find_tc_kernel(int form, int p);
+
 static thread_local std::string g_last_error;
 static int fail(int code, const std::string& msg) {
   g_last_error = msg;
@@ -84,6 +87,17 @@ int get_tables(DevState* st, int form, int p, int prec, TableEntry** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto key = std::make_tuple(form, p, prec);
   auto it = st->tables.find(key);
+  if (it == st->tables.end() && prec == 2) {
+    std::vector<uint32_t> words;
+    if (!tc_table_words(form, p, &words)) return fail(FEA_EINVAL, "no tensor-core table for this form/degree");
+    TableEntry te;
+    te.lay.total = (int)words.size();
+    const size_t bytes = words.size() * 4;
+    if (cudaMalloc(&te.dev, bytes) != cudaSuccess) return fail(FEA_ENOMEM, "table allocation failed");
+    const cudaError_t e = cudaMemcpy(te.dev, words.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(FEA_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    it = st->tables.emplace(key, te).first;
+  }
   if (it == st->tables.end()) {
     Tables t = make_tables(form, p);
     TableEntry te;
@@ -178,7 +192,11 @@ int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, boo
 static int make_plan_uncached(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch,
                               bool use_tuned) {
   if (!valid_fd(form, p)) return fail(FEA_EINVAL, "unsupported form/degree");
-  if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32) return fail(FEA_EINVAL, "unsupported precision");
+  if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32 && o.precision != FEA_PREC_BF16X2)
+    return fail(FEA_EINVAL, "unsupported precision");
+  // split-BF16 tensor-core contraction where a kernel exists (the dense, compute-bound
+  // Neo-Hookean tangent); the other (form, degree) run the FP32 contraction
+  const KernelInfo* tc = o.precision == FEA_PREC_BF16X2 && !batch ? find_tc_kernel(form, p) : nullptr;
   const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
   const size_t limit = st ? st->smem_optin : 232448;
   const size_t budget = o.smem_budget ? std::min(o.smem_budget, limit) : limit;
@@ -189,17 +207,23 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
     return fail(FEA_EINVAL, "pre-evaluation does not apply to this form (integrand not polynomial)");
   const int Q = rule_points(rule_index(form, p));
   const KernelInfo* k = batch ? find_batch_kernel(variant, form, p) : find_kernel(variant, form, p, prec, budget, Q);
+  if (tc && variant == tc->variant) k = tc;
   if (!k) return fail(FEA_EINVAL, "no kernel for this variant/form/degree/precision");
   int TE = o.tile;
   if (TE < 0) return fail(FEA_EINVAL, "negative tile");
   // tuned tiles were measured on the standalone kernels; the batch keeps its own rule
+  if (k == tc) {
+    // the tensor-core kernel's layout fixes its tile (9 columns of the 128-column MMA per element)
+    if (TE != 0 && TE != tc->pref_tile) return fail(FEA_EINVAL, "the tensor-core kernel runs tiles of exactly 14 elements");
+    TE = tc->pref_tile;
+  }
   if (TE == 0) TE = default_tile(variant, form, p, prec, k->max_tile, budget, Q, k->smem, use_tuned && !batch, k->pref_tile);
   if (TE < 1 || TE > k->max_tile) return fail(FEA_EINVAL, "tile out of range for this kernel");
   const size_t smem = k->smem(TE, Q);
   if (smem > budget) return fail(FEA_EINVAL, "tile does not fit the shared-memory budget (Constraint 2)");
   pl->k = k;
   pl->variant = variant;
-  pl->prec = prec;
+  pl->prec = k->prec;
   pl->tile = TE;
   pl->Q = Q;
   pl->smem = smem;
@@ -273,7 +297,8 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
       const int ceiling = (int)st->smem_optin - (int)fa.sharedSizeBytes;  // minus the kernel's static shared memory
       if ((int)smem_bytes > ceiling) return fail(FEA_EINVAL, "tile does not fit the device's shared memory");
       CUDA_TRY(cudaFuncSetAttribute(pl.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ceiling));
-      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, NT, smem_bytes));
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, pl.k->threads ? pl.k->threads : NT,
+                                                             smem_bytes));
       occ[key] = per_sm;
     } else {
       per_sm = it->second;
@@ -281,6 +306,7 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
   }
   if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with this tile");
   L->fn = pl.k->fn;
+  L->threads = pl.k->threads ? pl.k->threads : NT;
   L->grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
   L->smem = smem_bytes;
   L->q = q;
@@ -290,7 +316,7 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
 
 int issue_launch(PreparedLaunch& L, cudaStream_t stream) {
   void* args[] = {&L.q, &L.err};
-  CUDA_TRY(cudaLaunchKernel(L.fn, dim3(L.grid), dim3(NT), args, L.smem, stream));
+  CUDA_TRY(cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.threads), args, L.smem, stream));
   return FEA_OK;
 }
 
@@ -591,7 +617,7 @@ static int plan_impl(int form, int degree, const fea_options* opt, fea_plan_info
   OpCounts oc = op_counts(form, degree);
   info->variant = pl.variant;
   info->tile = pl.tile;
-  info->threads = NT;
+  info->threads = pl.k->threads ? pl.k->threads : NT;
   info->quad_points = pl.Q;
   info->ref_terms = pre_terms(form, degree);
   info->smem_bytes = pl.smem;

@@ -12,6 +12,7 @@ struct KernelInfo {
   int max_tile;                       // upper bound on elements per tile
   size_t (*smem)(int TE, int Q);      // dynamic shared memory for a tile of TE
   int pref_tile;                      // tile the thread layout is built for (0: none)
+  int threads = 0;                    // threads per CTA (0: NT)
 };
 
 // Registered by the kernel translation units.
@@ -21,6 +22,10 @@ extern const KernelInfo kSeKernels[];
 extern const int kNumSeKernels;
 extern const KernelInfo kNaiveKernels[];
 extern const int kNumNaiveKernels;
+
+// Tensor-core kernels (split-operand precisions): Neo-Hookean P2.
+extern const KernelInfo kTcKernels[];
+extern const int kNumTcKernels;
 
 extern const KernelInfo kPreTileF32[];
 extern const int kNumPreTileF32;

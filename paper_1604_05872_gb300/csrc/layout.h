@@ -45,6 +45,33 @@ FEA_HD inline TabLayout tab_layout(int Q, int ns, int r) {
   return t;
 }
 
+// Pair p of the upper triangle a <= b of an n x n grid of blocks, row by row:
+// (0,0), (0,1), ..., (0,n-1), (1,1), ...
+FEA_HD inline void sym_pair(int p, int n, int* a, int* b) {
+  int aa = 0;
+  while (aa < n && p >= n - aa) {
+    p -= n - aa;
+    ++aa;
+  }
+  *a = aa;
+  *b = aa + p;
+}
+
+// Device table of the tensor-core Neo-Hookean kernel, in 32-bit words: W [Q],
+// dphi [Q][ns][3] (float), then the split reference tables R_stack [128][K / 2]
+// (packed 16-bit pairs; row 2p = hi, 2p + 1 = lo part of the pair p = (a, b)).
+struct TcTabLayout {
+  int offW, offDphi, offR, total;
+};
+FEA_HD inline TcTabLayout tc_tab_layout(int Q, int ns, int K) {
+  TcTabLayout t{};
+  t.offW = 0;
+  t.offDphi = round_up(Q, 4);
+  t.offR = t.offDphi + round_up(Q * ns * 3, 4);
+  t.total = t.offR + 128 * (K / 2);
+  return t;
+}
+
 // One assembly request as the kernels see it.
 struct Req {
   const double* coords;

@@ -1,0 +1,510 @@
+// Neo-Hookean tangent stiffness on the tensor cores (tcgen05), split-BF16
+// operands with FP32 accumulation.
+//
+// Per quadrature point the tangent's integrand factors through the reference
+// gradients: with M_q = F^-T J^-T, K = J^-1 J^-T, s_q = w_q |det J| and
+// alpha_q = mu - lam ln det F,
+//
+//   A[(a,c),(b,d)] = sum_q sum_{k,l} H_q[(c,d),(k,l)] dPhi_a^k(X_q) dPhi_b^l(X_q),
+//   H_q[(c,d),(k,l)] = s alpha M[d][k] M[c][l] + s lam M[c][k] M[d][l] + delta_cd s mu K[k][l].
+//
+// This is the paper's pre-evaluation (Section 3.3, Algorithm 2) applied at each
+// quadrature point instead of over the whole integral (the integrand is not a
+// polynomial, so the point sum cannot be pre-evaluated): the reference tables
+// R_(a,b)[(q,k,l)] = dPhi_a^k(X_q) dPhi_b^l(X_q) are built once on the host, and
+// per element only the 9 x 9Q tensor H is formed.  The contraction over
+// (q, k, l) is one dense product per tile of TE elements:
+//
+//   D[128 x 128] = R_stack[128 x K] * H_tile[128 x K]^T
+//
+// rows of D: row 2p holds the BF16 "hi" part of R for the pair p = (a, b),
+// a <= b, row 2p + 1 the "lo" part (R - hi rounded to BF16); columns of D:
+// (element, c, d) = 9 e + 3 c + d.  H is split the same way and the two halves
+// run as two MMAs into the same accumulator, so D[2p] + D[2p + 1] is the sum of
+// all four products (hi + lo)(hi + lo) of the split operands, with FP32
+// accumulation in tensor memory.  The tangent is symmetric: the pair p gives
+// the 3 x 3 block (a, b) and, transposed, (b, a).
+//
+// Roles (one CTA per SM, persistent over tiles, 13 warps):
+//   warp 0      allocates tensor memory; one lane issues the MMAs;
+//   warps 1-4   epilogue: tensor memory -> FP32 staging (both blocks of each
+//               pair) -> coalesced 16-byte stores of the element matrices;
+//   warps 5-8   kinematics: tile inputs by bulk copy one tile ahead; FP64
+//               geometry per element; per (element, point) grad u (FP32), then
+//               F = I + grad u, its cofactors, det F and ln det F in FP64,
+//               M = F^-T J^-T, s, s alpha;
+//   warps 9-12  build H (one row (e, c, d) per thread), split into BF16 hi/lo.
+// R (128 rows x K/2 packed BF16 pairs) sits in tensor memory for the whole
+// launch; D is double-buffered in tensor memory.  Every mbarrier wait is
+// bounded; a role that gives up sets the error word, the others then give up
+// too, and the CTA waits for its copies and MMAs in flight before it frees the
+// tensor memory and leaves.
+#pragma once
+#include "common.cuh"
+#include "log_f64.cuh"
+#include "mbar.cuh"
+#include "tc.cuh"
+
+#include <cuda_bf16.h>
+
+namespace fea {
+
+template <int P>
+struct NhTc {
+  static constexpr int NS = nbasis_c(P);
+  static constexpr int N3 = 3 * NS;
+  static constexpr int NN = N3 * N3;
+  static constexpr int CLEN = 3 * NS;
+  static constexpr int NPAIR = NS * (NS + 1) / 2;
+  static_assert(2 * NPAIR <= 128, "the split reference tables must fit one 128-row MMA tile");
+  static constexpr int Q = (P + 1) * (P + 1) * (P + 1);  // collapsed rule, p + 1 points per direction
+  static constexpr int TE = 14;                          // elements per tile: 9 TE <= 128 columns
+  static constexpr int NCOL = 128;
+  static constexpr int KK = 9 * Q;
+  static constexpr int K = (KK + 15) / 16 * 16;
+  static constexpr int KU = K / 8;        // 16-byte core-matrix columns along K
+  static constexpr int KS = K / 16;       // MMA steps
+  static constexpr int NG = (KU + 8) / 9; // point groups of 8 (9 core-matrix columns each)
+  static_assert(8 * NG >= Q, "point groups must cover the rule");
+  static constexpr uint32_t LBO = 128, SBO = KU * 128;
+  static constexpr int HPART = NCOL * K * 2;  // bytes of one split part of H
+  static constexpr int EH = TE / 2;           // elements staged per epilogue half
+  static constexpr int PWF = 12;              // floats per (element, point): M[9], s, s alpha, pad
+  static constexpr int NTH = 416;
+  static constexpr int W_EPI = 1, W_KIN = 5, W_BLD = 9;
+  static constexpr int BAR_EPI = 1, BAR_KIN = 2;
+  static constexpr uint32_t COL_R = 256, TMEM_COLS = 512;
+  static_assert(COL_R + K / 2 <= TMEM_COLS, "tensor memory");
+
+  static constexpr size_t O_HHI = 0, O_HLO = HPART;
+  static constexpr size_t O_STAGE = 2 * (size_t)HPART;
+  static constexpr size_t O_PW = O_STAGE + round_up_sz((size_t)EH * NN * 4, 16);
+  static constexpr size_t PW_SLOT = (size_t)TE * Q * PWF * 4;
+  static constexpr size_t O_PWK = O_PW + 2 * PW_SLOT;
+  static constexpr size_t O_IN = O_PWK + 2 * (size_t)TE * 8 * 4;
+  static constexpr size_t IN_BUF = (size_t)TE * (12 + CLEN) * 8;  // coords, then displacement DOFs
+  static constexpr size_t O_UT = O_IN + 2 * IN_BUF;
+  static constexpr size_t O_GEO = O_UT + round_up_sz((size_t)TE * CLEN * 4, 16);
+  static constexpr size_t O_W = O_GEO + (size_t)TE * 12 * 4;
+  static constexpr size_t O_DPHI = O_W + round_up_sz((size_t)Q * 4, 16);
+  static constexpr size_t O_BAR = O_DPHI + round_up_sz((size_t)Q * NS * 3 * 4, 16);
+  static constexpr size_t SMEM = O_BAR + 256 + 1024;  // + alignment of the base to 1024 bytes
+  static_assert(O_IN % 16 == 0 && IN_BUF % 16 == 0 && (TE * 96) % 16 == 0, "bulk-copy alignment");
+
+  FEA_HD static int max_tile() { return TE; }
+  FEA_HD static int pref_tile() { return TE; }
+  FEA_HD static size_t smem(int, int) { return SMEM; }
+};
+
+struct NhTcBars {
+  uint64_t in_full[2], pw_full[2], pw_empty[2], h_full, h_empty, d_full[2], d_empty[2], done;
+  uint32_t tbase;
+};
+
+// (x, y) -> BF16 pair hi (x low) and the BF16 pair lo of the remainders.
+__device__ __forceinline__ void split_bf16x2(float x, float y, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  const float rx = x - __low2float(h), ry = y - __high2float(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(rx, ry);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// One half (EH elements) of a tile's epilogue: accumulator columns -> hi + lo
+// sum -> FP32 staging (both blocks of each pair) -> coalesced stores.  The last
+// half releases the accumulator buffer once its columns are read.
+template <int P, int HALF>
+__device__ __forceinline__ void nh_tc_epi_half(uint32_t dcol, int ne, bool writer, int base, int sc, int sd,
+                                               float* stage, const Req& q, int64_t e0, int et, int lane,
+                                               uint64_t* d_empty) {
+  using C = NhTc<P>;
+  constexpr int EH0 = HALF * C::EH;
+  constexpr int CH0 = (9 * EH0) / 16, CH1 = (9 * (EH0 + C::EH) + 15) / 16;
+  const int nh = ne - EH0 < C::EH ? ne - EH0 : C::EH;
+#pragma unroll
+  for (int ch = CH0; ch < CH1; ++ch) {
+    uint32_t r[16];
+    tmem_ld16(dcol + 16u * (uint32_t)ch, r);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = 16 * ch + j;
+      const int el = n / 9 - EH0;
+      if (el >= 0 && el < C::EH) {
+        const int cd = n % 9;
+        const float v = __uint_as_float(r[j]);
+        const float s = v + __shfl_xor_sync(0xffffffffu, v, 1);
+        if (writer && el < nh) stage[el * C::NN + base + (cd / 3) * sc + (cd % 3) * sd] = s;
+      }
+    }
+  }
+  if (HALF == 1) {
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(d_empty);
+  }
+  named_sync(C::BAR_EPI, 128);
+  if (nh > 0) {
+    const int64_t off = (e0 + EH0) * C::NN;  // a multiple of 4 entries
+    const int cnt = nh * C::NN;
+    if (q.out_f32) {
+      const float4* s4 = reinterpret_cast<const float4*>(stage);
+      float4* o4 = reinterpret_cast<float4*>(static_cast<float*>(q.out) + off);
+      for (int k = et; k < cnt / 4; k += 128) __stcs(o4 + k, s4[k]);
+    } else {
+      const float2* s2 = reinterpret_cast<const float2*>(stage);
+      double2* o2 = reinterpret_cast<double2*>(static_cast<double*>(q.out) + off);
+      for (int k = et; k < cnt / 2; k += 128) {
+        const float2 v = s2[k];
+        __stcs(o2 + k, make_double2(f2d(v.x), f2d(v.y)));
+      }
+    }
+  }
+  named_sync(C::BAR_EPI, 128);
+}
+
+template <int P>
+__global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned* err) {
+  using C = NhTc<P>;
+  extern __shared__ __align__(16) char smem_raw[];
+  if (C::SMEM > dynamic_smem_bytes()) {
+    if (threadIdx.x == 0) flag_error(err, ERR_LAUNCH);
+    return;
+  }
+  char* sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  NhTcBars* bars = reinterpret_cast<NhTcBars*>(sm + C::O_BAR);
+  float* sW = reinterpret_cast<float*>(sm + C::O_W);
+  float* sD = reinterpret_cast<float*>(sm + C::O_DPHI);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (q.E + C::TE - 1) / C::TE;
+  const float* tab = static_cast<const float*>(q.tab);
+  const TcTabLayout L = tc_tab_layout(C::Q, C::NS, C::K);
+  const float mu_c = d2f(q.coeffs[q.E * C::CLEN]), lam_c = d2f(q.coeffs[q.E * C::CLEN + 1]);
+  const float nan = __int_as_float(0x7fc00000);
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bars->in_full[i], 1);
+      mbar_init(&bars->pw_full[i], 4);
+      mbar_init(&bars->pw_empty[i], 4);
+      mbar_init(&bars->d_full[i], 1);
+      mbar_init(&bars->d_empty[i], 4);
+    }
+    mbar_init(&bars->h_full, 4);
+    mbar_init(&bars->h_empty, 1);
+    mbar_init(&bars->done, 1);
+    fence_barrier_init();
+  }
+  for (int i = tid; i < C::Q; i += C::NTH) sW[i] = tab[L.offW + i];
+  for (int i = tid; i < C::Q * C::NS * 3; i += C::NTH) sD[i] = tab[L.offDphi + i];
+  {
+    uint4* z = reinterpret_cast<uint4*>(sm);
+    for (int i = tid; i < 2 * C::HPART / 16; i += C::NTH) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (warp == 0) {
+    tmem_alloc(&bars->tbase, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = bars->tbase;
+
+  // reference tables into tensor memory: lane m = row m of R_stack, K / 2 packed columns
+  if (warp >= C::W_EPI && warp < C::W_KIN) {
+    const int qd = warp & 3, m = 32 * qd + lane;
+    const uint4* src = reinterpret_cast<const uint4*>(tab + L.offR) + (size_t)m * (C::K / 8);
+    for (int c0 = 0; c0 < C::K / 2; c0 += 16) {
+      uint32_t v[16];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint4 w = __ldg(src + c0 / 4 + j);
+        v[4 * j] = w.x;
+        v[4 * j + 1] = w.y;
+        v[4 * j + 2] = w.z;
+        v[4 * j + 3] = w.w;
+      }
+      tmem_st16(tb + ((uint32_t)(32 * qd) << 16) + C::COL_R + (uint32_t)c0, v);
+    }
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16kind(1u, 128u, (uint32_t)C::NCOL);
+      const uint32_t hhi = smem_addr(sm + C::O_HHI), hlo = smem_addr(sm + C::O_HLO);
+      bool ok = true;
+      int it = 0;
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        ok = mbar_wait(&bars->h_full, (unsigned)(it & 1));
+        if (ok && it >= 2) ok = mbar_wait(&bars->d_empty[buf], (unsigned)(((it >> 1) - 1) & 1));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t dt = tb + (uint32_t)buf * 128u;
+#pragma unroll 4
+        for (int j = 0; j < C::KS; ++j) {
+          const uint32_t at = tb + C::COL_R + 8u * (uint32_t)j;
+          mma_f16_ts(dt, at, smem_desc_kmajor(hhi + 2u * C::LBO * j, C::LBO, C::SBO), idesc, j > 0 ? 1u : 0u);
+          mma_f16_ts(dt, at, smem_desc_kmajor(hlo + 2u * C::LBO * j, C::LBO, C::SBO), idesc, 1u);
+        }
+        tc_commit(&bars->h_empty);
+        tc_commit(&bars->d_full[buf]);
+      }
+      if (!ok) flag_error(err, ERR_TIMEOUT);
+      tc_commit(&bars->done);
+      if (!mbar_wait(&bars->done, 0u)) flag_error(err, ERR_TIMEOUT);
+    }
+    __syncwarp();
+  } else if (warp < C::W_KIN) {
+    // -------------------------------------------------------------- epilogue
+    const int et = tid - 32 * C::W_EPI;
+    const int qd = warp & 3, m = 32 * qd + lane, p = m >> 1, hx = m & 1;
+    int a = 0, b = 0;
+    if (p < C::NPAIR) sym_pair(p, C::NS, &a, &b);
+    const bool writer = p < C::NPAIR && (hx == 0 || a != b);
+    // even lane: entry (3a + c, 3b + d); odd lane: the mirrored entry (3b + d, 3a + c)
+    const int base = hx == 0 ? 3 * a * C::N3 + 3 * b : 3 * b * C::N3 + 3 * a;
+    const int sc = hx == 0 ? C::N3 : 1, sd = hx == 0 ? 1 : C::N3;
+    float* stage = reinterpret_cast<float*>(sm + C::O_STAGE);
+    const uint32_t trow = tb + ((uint32_t)(32 * qd) << 16);
+    bool ok = true;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int buf = it & 1;
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
+      ok = named_and(C::BAR_EPI, 128, mbar_wait(&bars->d_full[buf], (unsigned)((it >> 1) & 1)));
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t dcol = trow + (uint32_t)buf * 128u;
+      nh_tc_epi_half<P, 0>(dcol, ne, writer, base, sc, sd, stage, q, e0, et, lane, &bars->d_empty[buf]);
+      nh_tc_epi_half<P, 1>(dcol, ne, writer, base, sc, sd, stage, q, e0, et, lane, &bars->d_empty[buf]);
+    }
+    if (!ok) flag_error(err, ERR_TIMEOUT);
+  } else if (warp < C::W_BLD) {
+    // ------------------------------------------------------------ kinematics
+    const int kt = tid - 32 * C::W_KIN;
+    float* ut = reinterpret_cast<float*>(sm + C::O_UT);
+    float* geo = reinterpret_cast<float*>(sm + C::O_GEO);
+    auto issue_inputs = [&](int64_t t, int ib) {
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
+      char* dst = sm + C::O_IN + (size_t)ib * C::IN_BUF;
+      mbar_expect_tx(&bars->in_full[ib], (unsigned)(ne * (12 + C::CLEN) * 8));
+      bulk_g2s(dst, q.coords + e0 * 12, (unsigned)(ne * 96), &bars->in_full[ib]);
+      bulk_g2s(dst + C::TE * 96, q.coeffs + e0 * C::CLEN, (unsigned)(ne * C::CLEN * 8), &bars->in_full[ib]);
+    };
+    int pending = -1;  // input buffer with a copy in flight (leader thread)
+    if (kt == 0 && blockIdx.x < ntiles) {
+      issue_inputs(blockIdx.x, 0);
+      pending = 0;
+    }
+    bool ok = true;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int slot = it & 1, ib = it & 1;
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
+      bool w = true;
+      if (it >= 2) w = mbar_wait(&bars->pw_empty[slot], (unsigned)(((it >> 1) - 1) & 1));
+      w = w && mbar_wait(&bars->in_full[ib], (unsigned)((it >> 1) & 1));
+      ok = named_and(C::BAR_KIN, 128, w);
+      if (!ok) break;
+      if (kt == 0) pending = -1;
+      // the other input buffer was last read before the barrier above: prefetch the next tile into it
+      if (kt == 0 && t + gridDim.x < ntiles) {
+        fence_proxy_async();
+        issue_inputs(t + gridDim.x, ib ^ 1);
+        pending = ib ^ 1;
+      }
+      const double* xs = reinterpret_cast<const double*>(sm + C::O_IN + (size_t)ib * C::IN_BUF);
+      const double* us = xs + C::TE * 12;
+      float* pw = reinterpret_cast<float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT);
+      float* pwk = reinterpret_cast<float*>(sm + C::O_PWK) + slot * C::TE * 8;
+      for (int i = kt; i < ne * C::CLEN; i += 128) ut[i] = d2f(us[i]);
+      if (kt < ne) {  // FP64 geometry of element kt
+        double adj[9];
+        const double det = geometry_fp64(xs + 12 * kt, adj);
+        const uint64_t bits = (uint64_t)__double_as_longlong(det);
+        const bool bad = ((bits << 1) == 0) || ((bits >> 52 & 0x7ff) == 0x7ff);
+        if (bad) flag_error(err, ERR_DEGENERATE);
+        const float df = d2f(det), inv = 1.0f / df;
+        float Ji[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ji[k] = d2f(adj[k]) * inv;
+        float* g = geo + 12 * kt;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) g[k] = bad ? nan : Ji[k];
+        g[9] = bad ? nan : fabsf(df);
+        const int kk0[6] = {0, 1, 2, 0, 0, 1}, kk1[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int x = kk0[k], y = kk1[k];
+          pwk[8 * kt + k] = bad ? nan : Ji[3 * x] * Ji[3 * y] + Ji[3 * x + 1] * Ji[3 * y + 1] + Ji[3 * x + 2] * Ji[3 * y + 2];
+        }
+      }
+      named_sync(C::BAR_KIN, 128);
+      for (int w2 = kt; w2 < ne * C::Q; w2 += 128) {
+        const int e = w2 / C::Q, qq = w2 - e * C::Q;
+        const float* Ji = geo + 12 * e;
+        const float* u = ut + C::CLEN * e;
+        const float* dp = sD + qq * C::NS * 3;
+        float gr[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) gr[k] = 0.f;
+#pragma unroll
+        for (int a = 0; a < C::NS; ++a) {
+          const float d0 = dp[3 * a], d1 = dp[3 * a + 1], d2 = dp[3 * a + 2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const float ui = u[3 * a + i];
+            gr[3 * i] = fmaf(ui, d0, gr[3 * i]);
+            gr[3 * i + 1] = fmaf(ui, d1, gr[3 * i + 1]);
+            gr[3 * i + 2] = fmaf(ui, d2, gr[3 * i + 2]);
+          }
+        }
+        float J[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) J[k] = Ji[k];
+        double F[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            F[3 * i + x] = f2d(gr[3 * i] * J[x] + gr[3 * i + 1] * J[3 + x] + gr[3 * i + 2] * J[6 + x]);
+        F[0] += 1.0;
+        F[4] += 1.0;
+        F[8] += 1.0;
+        double cof[9];  // det(F) F^-1
+        cof[0] = fma(F[4], F[8], -F[5] * F[7]);
+        cof[1] = fma(F[2], F[7], -F[1] * F[8]);
+        cof[2] = fma(F[1], F[5], -F[2] * F[4]);
+        cof[3] = fma(F[5], F[6], -F[3] * F[8]);
+        cof[4] = fma(F[0], F[8], -F[2] * F[6]);
+        cof[5] = fma(F[2], F[3], -F[0] * F[5]);
+        cof[6] = fma(F[3], F[7], -F[4] * F[6]);
+        cof[7] = fma(F[1], F[6], -F[0] * F[7]);
+        cof[8] = fma(F[0], F[4], -F[1] * F[3]);
+        const double dF = fma(F[0], cof[0], fma(F[1], cof[3], F[2] * cof[6]));
+        const uint32_t dhi = (uint32_t)__double2hiint(dF);
+        const bool bad = (int)dhi <= 0 || (dhi >> 20) >= 0x7ffu;  // det F <= 0 (or tiny), inf or NaN
+        if (bad) flag_error(err, ERR_DEGENERATE);
+        // the cancellation-prone cofactors, det F and ln det F are FP64; F^-1 = cof / det F
+        // is a well-conditioned scaling done after rounding to FP32
+        const float idF = 1.0f / d2f(dF);
+        const float lnJ = d2f(log_f64(dF));
+        float Fi[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fi[k] = d2f(cof[k]) * idF;  // Fi[3 I + c] = (F^-1)[I][c]
+        float Mq[9];                                              // M[c][k] = sum_I (F^-1)[I][c] (J^-1)[k][I]
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Mq[3 * c + k] = Fi[c] * J[3 * k] + Fi[3 + c] * J[3 * k + 1] + Fi[6 + c] * J[3 * k + 2];
+        const float s = sW[qq] * Ji[9];
+        const float sa = s * (mu_c - lam_c * lnJ);
+        float4* o = reinterpret_cast<float4*>(pw + (size_t)w2 * C::PWF);
+        o[0] = bad ? make_float4(nan, nan, nan, nan) : make_float4(Mq[0], Mq[1], Mq[2], Mq[3]);
+        o[1] = bad ? make_float4(nan, nan, nan, nan) : make_float4(Mq[4], Mq[5], Mq[6], Mq[7]);
+        o[2] = bad ? make_float4(nan, nan, nan, 0.f) : make_float4(Mq[8], s, sa, 0.f);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->pw_full[slot]);
+    }
+    if (!ok) flag_error(err, ERR_TIMEOUT);
+    // a prefetch issued before giving up (for iteration `it`) must land before the CTA leaves
+    if (kt == 0 && pending >= 0) mbar_wait(&bars->in_full[pending], (unsigned)((it >> 1) & 1));
+  } else {
+    // ----------------------------------------------------------- H builders
+    const int bt = tid - 32 * C::W_BLD;  // the H row (column of D) of this thread
+    const int e = bt / 9, cd = bt - 9 * (bt / 9), c = cd / 3, d = cd - 3 * (cd / 3);
+    const float dmu = c == d ? mu_c : 0.f;
+    char* hhi = sm + C::O_HHI + (size_t)(bt >> 3) * C::SBO + (size_t)(bt & 7) * 16;
+    char* hlo = sm + C::O_HLO + (size_t)(bt >> 3) * C::SBO + (size_t)(bt & 7) * 16;
+    bool ok = true;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int slot = it & 1;
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
+      unsigned w = 1;
+      if (lane == 0) {
+        w = mbar_wait(&bars->pw_full[slot], (unsigned)((it >> 1) & 1));
+        if (w && it >= 1) w = mbar_wait(&bars->h_empty, (unsigned)((it - 1) & 1));
+      }
+      ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+      if (!ok) break;
+      if (e < ne) {
+        const float* pwe = reinterpret_cast<const float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT) + (size_t)e * C::Q * C::PWF;
+        const float* kp = reinterpret_cast<const float*>(sm + C::O_PWK) + slot * C::TE * 8 + 8 * e;
+        const float4 k0 = *reinterpret_cast<const float4*>(kp), k1 = *reinterpret_cast<const float4*>(kp + 4);
+        const float Km[9] = {k0.x, k0.w, k1.x, k0.w, k0.y, k1.y, k1.x, k1.y, k0.z};
+        for (int g = 0; g < C::NG; ++g) {
+          float h[72];
+#pragma unroll
+          for (int qi = 0; qi < 8; ++qi) {
+            const int qq = 8 * g + qi;
+            if (qq < C::Q) {
+              const float4 A0 = *reinterpret_cast<const float4*>(pwe + qq * C::PWF);
+              const float4 A1 = *reinterpret_cast<const float4*>(pwe + qq * C::PWF + 4);
+              const float4 A2 = *reinterpret_cast<const float4*>(pwe + qq * C::PWF + 8);
+              const float M[9] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w, A2.x};
+              const float s = A2.y, sa = A2.z;
+              const float sl = s * lam_c, smu = s * dmu;
+              float Mc[3], Md[3];
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                Mc[k] = c == 0 ? M[k] : (c == 1 ? M[3 + k] : M[6 + k]);
+                Md[k] = d == 0 ? M[k] : (d == 1 ? M[3 + k] : M[6 + k]);
+              }
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const float pd = sa * Md[k], lc = sl * Mc[k];
+#pragma unroll
+                for (int l = 0; l < 3; ++l) h[9 * qi + 3 * k + l] = fmaf(pd, Mc[l], fmaf(lc, Md[l], smu * Km[3 * k + l]));
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 9; ++k) h[9 * qi + k] = 0.f;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            const int uidx = 9 * g + i;
+            if (uidx < C::KU) {
+              uint4 vh, vl;
+              split_bf16x2(h[8 * i], h[8 * i + 1], vh.x, vl.x);
+              split_bf16x2(h[8 * i + 2], h[8 * i + 3], vh.y, vl.y);
+              split_bf16x2(h[8 * i + 4], h[8 * i + 5], vh.z, vl.z);
+              split_bf16x2(h[8 * i + 6], h[8 * i + 7], vh.w, vl.w);
+              *reinterpret_cast<uint4*>(hhi + (size_t)uidx * C::LBO) = vh;
+              *reinterpret_cast<uint4*>(hlo + (size_t)uidx * C::LBO) = vl;
+            }
+          }
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars->h_full);
+        mbar_arrive(&bars->pw_empty[slot]);
+      }
+    }
+    if (!ok) flag_error(err, ERR_TIMEOUT);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tb, C::TMEM_COLS);
+  }
+}
+
+}  // namespace fea

@@ -23,6 +23,7 @@ struct Plan {
 struct PreparedLaunch {
   const void* fn = nullptr;
   unsigned grid = 0;
+  int threads = NT;
   size_t smem = 0;
   Req q{};
   unsigned* err = nullptr;
