@@ -51,6 +51,26 @@ __device__ __forceinline__ float d2f(double x) {
   return __uint_as_float(sign | f);
 }
 
+// Cheaper conversions for values known to be finite and well scaled (the
+// Neo-Hookean kinematics), where the exact special cases of f2d/d2f do not
+// matter: f2d_normal widens exactly every normal float and zero (FP32 math here
+// flushes subnormals); d2f_rz rounds toward zero, gives a signed zero below the
+// float range and NaN above it (callers mark such points degenerate anyway).
+__device__ __forceinline__ double f2d_normal(float f) {
+  const uint32_t u = __float_as_uint(f), a = u & 0x7fffffffu;
+  const uint32_t hi = a == 0u ? 0u : (a >> 3) + 0x38000000u;
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
+}
+__device__ __forceinline__ float d2f_rz(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  // hi << 3 | lo >> 29: the exponent's low 8 bits land on 23..30, the top 23 mantissa bits below;
+  // for exponents 897..1150 the float exponent is those 8 bits with the top one flipped
+  const uint32_t t = __funnelshift_l(lo, hi, 3);
+  const uint32_t e = (hi >> 20) & 0x7ffu, sign = hi & 0x80000000u;
+  const uint32_t f = ((t & 0x7fffffffu) ^ 0x40000000u) | sign;
+  return __uint_as_float(e - 897u < 254u ? f : (e < 897u ? sign : 0x7fc00000u));
+}
+
 template <typename T> __device__ __forceinline__ T from_double(double x);
 template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f(x); }

@@ -47,6 +47,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
+// Bounded wait that lets the warp sleep in the barrier (try_wait with a
+// suspend-time hint) instead of spinning, for waits that may last a whole tile:
+// gives up after about `limit_ns` of wall time (false).
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, unsigned parity, uint64_t limit_ns = 2000000000ull) {
+  const unsigned a = smem_addr(bar);
+  uint64_t start = 0;
+  for (long it = 0; it < (1L << 24); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(20000u)
+        : "memory");
+    if (done) return true;
+    if (it == 0) start = global_ns();
+    else if (global_ns() - start > limit_ns) return false;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }

@@ -25,15 +25,21 @@
 // accumulation in tensor memory.  The tangent is symmetric: the pair p gives
 // the 3 x 3 block (a, b) and, transposed, (b, a).
 //
-// Roles (one CTA per SM, persistent over tiles, 13 warps):
-//   warp 0      allocates tensor memory; one lane issues the MMAs;
-//   warps 1-4   epilogue: tensor memory -> FP32 staging (both blocks of each
-//               pair) -> coalesced 16-byte stores of the element matrices;
-//   warps 5-8   kinematics: tile inputs by bulk copy one tile ahead; FP64
-//               geometry per element; per (element, point) grad u (FP32), then
-//               F = I + grad u, its cofactors, det F and ln det F in FP64,
-//               M = F^-T J^-T, s, s alpha;
-//   warps 9-12  build H (one row (e, c, d) per thread), split into BF16 hi/lo.
+// The q-independent term delta_cd s mu K sums to mu |det J| K[k][l] times the
+// point-summed table sum_q w_q dPhi_a^k dPhi_b^l: it enters as one extra
+// "point" (9 more columns of K, in the padding of the MMA's K extent), so the
+// per-point H carries only the two M M terms.
+//
+// Roles (one CTA per SM, persistent over tiles, 21 warps):
+//   warp 0       allocates tensor memory; one lane issues the MMAs;
+//   warps 1-4    epilogue: tensor memory -> FP32 staging (both blocks of each
+//                pair) -> coalesced 16-byte stores of the element matrices;
+//   warps 5-12   kinematics, two groups of four taking alternate tiles: tile
+//                inputs by bulk copy one tile ahead; FP64 geometry per element;
+//                per (element, point) grad u (FP32), then F = I + grad u, its
+//                cofactors, det F and ln det F in FP64, M = F^-T J^-T, s, s alpha;
+//   warps 13-20  build H, one row (e, c, d) per thread, two groups of four
+//                taking half of the points each; split into BF16 hi/lo.
 // R (128 rows x K/2 packed BF16 pairs) sits in tensor memory for the whole
 // launch; D is double-buffered in tensor memory.  Every mbarrier wait is
 // bounded; a role that gives up sets the error word, the others then give up
@@ -60,36 +66,45 @@ struct NhTc {
   static constexpr int Q = (P + 1) * (P + 1) * (P + 1);  // collapsed rule, p + 1 points per direction
   static constexpr int TE = 14;                          // elements per tile: 9 TE <= 128 columns
   static constexpr int NCOL = 128;
-  static constexpr int KK = 9 * Q;
+  static constexpr int KK = 9 * (Q + 1);                 // the points and the point-summed term
   static constexpr int K = (KK + 15) / 16 * 16;
-  static constexpr int KU = K / 8;        // 16-byte core-matrix columns along K
-  static constexpr int KS = K / 16;       // MMA steps
-  static constexpr int NG = (KU + 8) / 9; // point groups of 8 (9 core-matrix columns each)
-  static_assert(8 * NG >= Q, "point groups must cover the rule");
+  static constexpr int KU = K / 8;          // 16-byte core-matrix columns along K
+  static constexpr int KS = K / 16;         // MMA steps
+  static constexpr int NG = (KU + 8) / 9;   // groups of 8 points (9 core-matrix columns each)
+  static_assert(8 * NG >= Q + 1 && NG % 2 == 0, "point groups must cover the rule, two builder halves");
   static constexpr uint32_t LBO = 128, SBO = KU * 128;
   static constexpr int HPART = NCOL * K * 2;  // bytes of one split part of H
   static constexpr int EH = TE / 2;           // elements staged per epilogue half
-  static constexpr int PWF = 12;              // floats per (element, point): M[9], s, s alpha, pad
-  static constexpr int NTH = 416;
-  static constexpr int W_EPI = 1, W_KIN = 5, W_BLD = 9;
-  static constexpr int BAR_EPI = 1, BAR_KIN = 2;
+  // pointwise data: M rows as float4 (12 floats per point), element records padded so that
+  // neighbouring elements' rows fall on different banks; (s, s alpha) per point; per element
+  // mu |det J| K (9 floats, padded to 12)
+  static constexpr int PW_E = Q * 12 + ((12 - (Q * 12) % 32) + 32) % 32;
+  static constexpr int NTH = 672;
+  static constexpr int W_EPI = 1, W_KIN = 5, W_BLD = 13;
+  static constexpr int BAR_EPI = 1, BAR_KIN = 2;  // kinematics groups use 2 and 3
   static constexpr uint32_t COL_R = 256, TMEM_COLS = 512;
   static_assert(COL_R + K / 2 <= TMEM_COLS, "tensor memory");
 
   static constexpr size_t O_HHI = 0, O_HLO = HPART;
   static constexpr size_t O_STAGE = 2 * (size_t)HPART;
   static constexpr size_t O_PW = O_STAGE + round_up_sz((size_t)EH * NN * 4, 16);
-  static constexpr size_t PW_SLOT = (size_t)TE * Q * PWF * 4;
-  static constexpr size_t O_PWK = O_PW + 2 * PW_SLOT;
-  static constexpr size_t O_IN = O_PWK + 2 * (size_t)TE * 8 * 4;
+  static constexpr size_t PW_SLOT = (size_t)TE * PW_E * 4;
+  static constexpr size_t O_PWS = O_PW + 2 * PW_SLOT;
+  static constexpr size_t PWS_SLOT = (size_t)TE * Q * 8;
+  static constexpr size_t O_PWK = O_PWS + 2 * PWS_SLOT;
+  static constexpr size_t O_IN = O_PWK + 2 * (size_t)TE * 12 * 4;
   static constexpr size_t IN_BUF = (size_t)TE * (12 + CLEN) * 8;  // coords, then displacement DOFs
-  static constexpr size_t O_UT = O_IN + 2 * IN_BUF;
-  static constexpr size_t O_GEO = O_UT + round_up_sz((size_t)TE * CLEN * 4, 16);
-  static constexpr size_t O_W = O_GEO + (size_t)TE * 12 * 4;
-  static constexpr size_t O_DPHI = O_W + round_up_sz((size_t)Q * 4, 16);
-  static constexpr size_t O_BAR = O_DPHI + round_up_sz((size_t)Q * NS * 3 * 4, 16);
+  static constexpr int RS = 36;  // floats per row of u and of dPhi: 16-byte loads of neighbouring rows hit other banks
+  static constexpr size_t O_UT = O_IN + 2 * IN_BUF;                // per group: u as float [TE][RS]
+  static constexpr size_t O_GEO = O_UT + 2 * (size_t)TE * RS * 4;  // per group: J^-1, |det J| [TE][12]
+  static constexpr size_t O_W = O_GEO + 2 * (size_t)TE * 12 * 4;
+  static constexpr size_t O_DPHI = O_W + round_up_sz((size_t)Q * 4, 16);  // [Q][RS]: dPhi_a^k at 3 a + k
+  static constexpr size_t O_BAR = O_DPHI + (size_t)Q * RS * 4;
   static constexpr size_t SMEM = O_BAR + 256 + 1024;  // + alignment of the base to 1024 bytes
   static_assert(O_IN % 16 == 0 && IN_BUF % 16 == 0 && (TE * 96) % 16 == 0, "bulk-copy alignment");
+  static_assert(O_PW % 16 == 0 && O_PWS % 16 == 0 && O_PWK % 16 == 0 && O_UT % 16 == 0 && O_DPHI % 16 == 0,
+                "vector alignment");
+  static_assert(CLEN <= 32 && NS * 3 <= 32, "padded rows");
 
   FEA_HD static int max_tile() { return TE; }
   FEA_HD static int pref_tile() { return TE; }
@@ -163,6 +178,53 @@ __device__ __forceinline__ void nh_tc_epi_half(uint32_t dcol, int ne, bool write
   named_sync(C::BAR_EPI, 128);
 }
 
+// Points 8 G .. 8 G + 7 of the H row (e, c, d), i.e. K columns 72 G .. 72 G + 71
+// (kk = 9 q + 3 k + l; point Q is the point-summed term, later ones are zero),
+// split into BF16 hi and lo parts: 9 core-matrix columns of each, each stored as
+// soon as its 8 values exist (column i is complete after point i, column 8 after point 7).
+template <int P, int G>
+__device__ __forceinline__ void nh_tc_build_group(const float* pwe, const float2* pws, const float* pwk, int c,
+                                                  int d, float lam, char* hhi, char* hlo) {
+  using C = NhTc<P>;
+  float h[72];
+#pragma unroll
+  for (int qi = 0; qi < 8; ++qi) {
+    const int q = 8 * G + qi;
+    if (q < C::Q) {
+      const float4 mc = *reinterpret_cast<const float4*>(pwe + 12 * q + 4 * c);
+      const float4 md = *reinterpret_cast<const float4*>(pwe + 12 * q + 4 * d);
+      const float2 ss = pws[q];  // (s, s alpha)
+      const float sl = ss.x * lam;
+      const float Mc[3] = {mc.x, mc.y, mc.z}, Md[3] = {md.x, md.y, md.z};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float pd = ss.y * Md[k], lc = sl * Mc[k];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) h[9 * qi + 3 * k + l] = fmaf(pd, Mc[l], lc * Md[l]);
+      }
+    } else if (q == C::Q) {
+#pragma unroll
+      for (int kl = 0; kl < 9; ++kl) h[9 * qi + kl] = c == d ? pwk[kl] : 0.f;
+    } else {
+#pragma unroll
+      for (int kl = 0; kl < 9; ++kl) h[9 * qi + kl] = 0.f;
+    }
+#pragma unroll
+    for (int i = qi; i <= (qi == 7 ? 8 : qi); ++i) {
+      const int uidx = 9 * G + i;
+      if (uidx < C::KU) {
+        uint4 vh, vl;
+        split_bf16x2(h[8 * i], h[8 * i + 1], vh.x, vl.x);
+        split_bf16x2(h[8 * i + 2], h[8 * i + 3], vh.y, vl.y);
+        split_bf16x2(h[8 * i + 4], h[8 * i + 5], vh.z, vl.z);
+        split_bf16x2(h[8 * i + 6], h[8 * i + 7], vh.w, vl.w);
+        *reinterpret_cast<uint4*>(hhi + (size_t)uidx * C::LBO) = vh;
+        *reinterpret_cast<uint4*>(hlo + (size_t)uidx * C::LBO) = vl;
+      }
+    }
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned* err) {
   using C = NhTc<P>;
@@ -186,20 +248,25 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars->in_full[i], 1);
       mbar_init(&bars->pw_full[i], 4);
-      mbar_init(&bars->pw_empty[i], 4);
+      mbar_init(&bars->pw_empty[i], 8);
       mbar_init(&bars->d_full[i], 1);
       mbar_init(&bars->d_empty[i], 4);
     }
-    mbar_init(&bars->h_full, 4);
+    mbar_init(&bars->h_full, 8);
     mbar_init(&bars->h_empty, 1);
     mbar_init(&bars->done, 1);
     fence_barrier_init();
   }
   for (int i = tid; i < C::Q; i += C::NTH) sW[i] = tab[L.offW + i];
-  for (int i = tid; i < C::Q * C::NS * 3; i += C::NTH) sD[i] = tab[L.offDphi + i];
+  for (int i = tid; i < C::Q * C::RS; i += C::NTH) {
+    const int qq = i / C::RS, j = i - qq * C::RS;
+    sD[i] = j < C::NS * 3 ? tab[L.offDphi + qq * C::NS * 3 + j] : 0.f;
+  }
   {
     uint4* z = reinterpret_cast<uint4*>(sm);
     for (int i = tid; i < 2 * C::HPART / 16; i += C::NTH) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    float* u = reinterpret_cast<float*>(sm + C::O_UT);
+    for (int i = tid; i < 2 * C::TE * C::RS; i += C::NTH) u[i] = 0.f;
   }
   if (warp == 0) {
     tmem_alloc(&bars->tbase, C::TMEM_COLS);
@@ -212,7 +279,7 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
   const uint32_t tb = bars->tbase;
 
   // reference tables into tensor memory: lane m = row m of R_stack, K / 2 packed columns
-  if (warp >= C::W_EPI && warp < C::W_KIN) {
+  if (warp >= C::W_EPI && warp < C::W_EPI + 4) {
     const int qd = warp & 3, m = 32 * qd + lane;
     const uint4* src = reinterpret_cast<const uint4*>(tab + L.offR) + (size_t)m * (C::K / 8);
     for (int c0 = 0; c0 < C::K / 2; c0 += 16) {
@@ -242,8 +309,8 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       int it = 0;
       for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int buf = it & 1;
-        ok = mbar_wait(&bars->h_full, (unsigned)(it & 1));
-        if (ok && it >= 2) ok = mbar_wait(&bars->d_empty[buf], (unsigned)(((it >> 1) - 1) & 1));
+        ok = mbar_wait_sleep(&bars->h_full, (unsigned)(it & 1));
+        if (ok && it >= 2) ok = mbar_wait_sleep(&bars->d_empty[buf], (unsigned)(((it >> 1) - 1) & 1));
         if (!ok) break;
         tc_fence_after();
         const uint32_t dt = tb + (uint32_t)buf * 128u;
@@ -258,7 +325,7 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       }
       if (!ok) flag_error(err, ERR_TIMEOUT);
       tc_commit(&bars->done);
-      if (!mbar_wait(&bars->done, 0u)) flag_error(err, ERR_TIMEOUT);
+      if (!mbar_wait_sleep(&bars->done, 0u)) flag_error(err, ERR_TIMEOUT);
     }
     __syncwarp();
   } else if (warp < C::W_KIN) {
@@ -279,7 +346,7 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       const int buf = it & 1;
       const int64_t e0 = t * C::TE;
       const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
-      ok = named_and(C::BAR_EPI, 128, mbar_wait(&bars->d_full[buf], (unsigned)((it >> 1) & 1)));
+      ok = named_and(C::BAR_EPI, 128, mbar_wait_sleep(&bars->d_full[buf], (unsigned)((it >> 1) & 1)));
       if (!ok) break;
       tc_fence_after();
       const uint32_t dcol = trow + (uint32_t)buf * 128u;
@@ -289,45 +356,45 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
     if (!ok) flag_error(err, ERR_TIMEOUT);
   } else if (warp < C::W_BLD) {
     // ------------------------------------------------------------ kinematics
-    const int kt = tid - 32 * C::W_KIN;
-    float* ut = reinterpret_cast<float*>(sm + C::O_UT);
-    float* geo = reinterpret_cast<float*>(sm + C::O_GEO);
-    auto issue_inputs = [&](int64_t t, int ib) {
+    const int gk = (warp - C::W_KIN) >> 2;  // group gk takes the iterations gk, gk + 2, ...
+    const int kt = tid - 32 * C::W_KIN - 128 * gk;
+    const int bar_id = C::BAR_KIN + gk;
+    float* ut = reinterpret_cast<float*>(sm + C::O_UT) + gk * C::TE * C::RS;
+    float* geo = reinterpret_cast<float*>(sm + C::O_GEO) + gk * C::TE * 12;
+    char* inb = sm + C::O_IN + (size_t)gk * C::IN_BUF;
+    float* pw = reinterpret_cast<float*>(sm + C::O_PW + (size_t)gk * C::PW_SLOT);
+    float2* pws = reinterpret_cast<float2*>(sm + C::O_PWS + (size_t)gk * C::PWS_SLOT);
+    float* pwk = reinterpret_cast<float*>(sm + C::O_PWK) + gk * C::TE * 12;
+    auto issue_inputs = [&](int64_t t) {
       const int64_t e0 = t * C::TE;
       const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
-      char* dst = sm + C::O_IN + (size_t)ib * C::IN_BUF;
-      mbar_expect_tx(&bars->in_full[ib], (unsigned)(ne * (12 + C::CLEN) * 8));
-      bulk_g2s(dst, q.coords + e0 * 12, (unsigned)(ne * 96), &bars->in_full[ib]);
-      bulk_g2s(dst + C::TE * 96, q.coeffs + e0 * C::CLEN, (unsigned)(ne * C::CLEN * 8), &bars->in_full[ib]);
+      mbar_expect_tx(&bars->in_full[gk], (unsigned)(ne * (12 + C::CLEN) * 8));
+      bulk_g2s(inb, q.coords + e0 * 12, (unsigned)(ne * 96), &bars->in_full[gk]);
+      bulk_g2s(inb + C::TE * 96, q.coeffs + e0 * C::CLEN, (unsigned)(ne * C::CLEN * 8), &bars->in_full[gk]);
     };
-    int pending = -1;  // input buffer with a copy in flight (leader thread)
-    if (kt == 0 && blockIdx.x < ntiles) {
-      issue_inputs(blockIdx.x, 0);
-      pending = 0;
+    int pending = 0;  // a copy in flight into this group's input buffer (leader thread)
+    const int64_t t_first = blockIdx.x + (int64_t)gk * gridDim.x;
+    if (kt == 0 && t_first < ntiles) {
+      issue_inputs(t_first);
+      pending = 1;
     }
     bool ok = true;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-      const int slot = it & 1, ib = it & 1;
+    int it = gk;
+    for (int64_t t = t_first; t < ntiles; t += 2 * (int64_t)gridDim.x, it += 2) {
       const int64_t e0 = t * C::TE;
       const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       bool w = true;
-      if (it >= 2) w = mbar_wait(&bars->pw_empty[slot], (unsigned)(((it >> 1) - 1) & 1));
-      w = w && mbar_wait(&bars->in_full[ib], (unsigned)((it >> 1) & 1));
-      ok = named_and(C::BAR_KIN, 128, w);
+      if (it >= 2) w = mbar_wait_sleep(&bars->pw_empty[gk], (unsigned)(((it >> 1) - 1) & 1));
+      w = w && mbar_wait_sleep(&bars->in_full[gk], (unsigned)((it >> 1) & 1));
+      ok = named_and(bar_id, 128, w);
       if (!ok) break;
-      if (kt == 0) pending = -1;
-      // the other input buffer was last read before the barrier above: prefetch the next tile into it
-      if (kt == 0 && t + gridDim.x < ntiles) {
-        fence_proxy_async();
-        issue_inputs(t + gridDim.x, ib ^ 1);
-        pending = ib ^ 1;
-      }
-      const double* xs = reinterpret_cast<const double*>(sm + C::O_IN + (size_t)ib * C::IN_BUF);
+      if (kt == 0) pending = 0;
+      const double* xs = reinterpret_cast<const double*>(inb);
       const double* us = xs + C::TE * 12;
-      float* pw = reinterpret_cast<float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT);
-      float* pwk = reinterpret_cast<float*>(sm + C::O_PWK) + slot * C::TE * 8;
-      for (int i = kt; i < ne * C::CLEN; i += 128) ut[i] = d2f(us[i]);
+      for (int i = kt; i < ne * C::CLEN; i += 128) {
+        const int e = i / C::CLEN;
+        ut[e * C::RS + (i - e * C::CLEN)] = d2f(us[i]);
+      }
       if (kt < ne) {  // FP64 geometry of element kt
         double adj[9];
         const double det = geometry_fp64(xs + 12 * kt, adj);
@@ -342,42 +409,63 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
 #pragma unroll
         for (int k = 0; k < 9; ++k) g[k] = bad ? nan : Ji[k];
         g[9] = bad ? nan : fabsf(df);
-        const int kk0[6] = {0, 1, 2, 0, 0, 1}, kk1[6] = {0, 1, 2, 1, 2, 2};
+        const float mdet = mu_c * fabsf(df);  // the point-summed term: mu |det J| J^-1 J^-T
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          const int x = kk0[k], y = kk1[k];
-          pwk[8 * kt + k] = bad ? nan : Ji[3 * x] * Ji[3 * y] + Ji[3 * x + 1] * Ji[3 * y + 1] + Ji[3 * x + 2] * Ji[3 * y + 2];
-        }
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            pwk[12 * kt + 3 * k + l] =
+                bad ? nan : mdet * (Ji[3 * k] * Ji[3 * l] + Ji[3 * k + 1] * Ji[3 * l + 1] + Ji[3 * k + 2] * Ji[3 * l + 2]);
       }
-      named_sync(C::BAR_KIN, 128);
+      named_sync(bar_id, 128);
+      // this group's input buffer has been read: prefetch the group's next tile into it
+      if (kt == 0 && t + 2 * (int64_t)gridDim.x < ntiles) {
+        fence_proxy_async();
+        issue_inputs(t + 2 * (int64_t)gridDim.x);
+        pending = 1;
+      }
       for (int w2 = kt; w2 < ne * C::Q; w2 += 128) {
         const int e = w2 / C::Q, qq = w2 - e * C::Q;
-        const float* Ji = geo + 12 * e;
-        const float* u = ut + C::CLEN * e;
-        const float* dp = sD + qq * C::NS * 3;
-        float gr[9];
+        float J[12];
+        {
+          const float4* j4 = reinterpret_cast<const float4*>(geo + 12 * e);
+          const float4 a0 = j4[0], a1 = j4[1], a2 = j4[2];
+          J[0] = a0.x; J[1] = a0.y; J[2] = a0.z; J[3] = a0.w;
+          J[4] = a1.x; J[5] = a1.y; J[6] = a1.z; J[7] = a1.w;
+          J[8] = a2.x; J[9] = a2.y; J[10] = a2.z; J[11] = a2.w;
+        }
+        float uv[32];  // u_a[i] at 3 a + i
+        {
+          const float4* u4 = reinterpret_cast<const float4*>(ut + C::RS * e);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) gr[k] = 0.f;
-#pragma unroll
-        for (int a = 0; a < C::NS; ++a) {
-          const float d0 = dp[3 * a], d1 = dp[3 * a + 1], d2 = dp[3 * a + 2];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const float ui = u[3 * a + i];
-            gr[3 * i] = fmaf(ui, d0, gr[3 * i]);
-            gr[3 * i + 1] = fmaf(ui, d1, gr[3 * i + 1]);
-            gr[3 * i + 2] = fmaf(ui, d2, gr[3 * i + 2]);
+          for (int v = 0; v < 8; ++v) {
+            const float4 uu = u4[v];
+            uv[4 * v] = uu.x; uv[4 * v + 1] = uu.y; uv[4 * v + 2] = uu.z; uv[4 * v + 3] = uu.w;
           }
         }
-        float J[9];
+        float gr[9];  // gr[3 i + k] = sum_a u_a[i] dPhi_a^k
 #pragma unroll
-        for (int k = 0; k < 9; ++k) J[k] = Ji[k];
-        double F[9];
+        for (int k = 0; k < 9; ++k) gr[k] = 0.f;
+        const float4* d4 = reinterpret_cast<const float4*>(sD + C::RS * qq);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const float4 dd = d4[v];
+          const float dv[4] = {dd.x, dd.y, dd.z, dd.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = 4 * v + j;  // dPhi_a^k with a = r / 3, k = r % 3
+            if (r < C::NS * 3) {
+#pragma unroll
+              for (int i = 0; i < 3; ++i) gr[3 * i + r % 3] = fmaf(uv[3 * (r / 3) + i], dv[j], gr[3 * i + r % 3]);
+            }
+          }
+        }
+        double F[9];  // F = I + grad u, grad u = gr J^-1 (FP32), widened exactly
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
           for (int x = 0; x < 3; ++x)
-            F[3 * i + x] = f2d(gr[3 * i] * J[x] + gr[3 * i + 1] * J[3 + x] + gr[3 * i + 2] * J[6 + x]);
+            F[3 * i + x] = f2d_normal(gr[3 * i] * J[x] + gr[3 * i + 1] * J[3 + x] + gr[3 * i + 2] * J[6 + x]);
         F[0] += 1.0;
         F[4] += 1.0;
         F[8] += 1.0;
@@ -397,36 +485,38 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
         if (bad) flag_error(err, ERR_DEGENERATE);
         // the cancellation-prone cofactors, det F and ln det F are FP64; F^-1 = cof / det F
         // is a well-conditioned scaling done after rounding to FP32
-        const float idF = 1.0f / d2f(dF);
-        const float lnJ = d2f(log_f64(dF));
-        float Fi[9];
+        const float idF = __frcp_rn(d2f_rz(dF));
+        const float lnJ = d2f_rz(log_f64(dF));
+        float Fi[9];  // Fi[3 I + c] = (F^-1)[I][c]
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Fi[k] = d2f(cof[k]) * idF;  // Fi[3 I + c] = (F^-1)[I][c]
-        float Mq[9];                                              // M[c][k] = sum_I (F^-1)[I][c] (J^-1)[k][I]
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) Mq[3 * c + k] = Fi[c] * J[3 * k] + Fi[3 + c] * J[3 * k + 1] + Fi[6 + c] * J[3 * k + 2];
-        const float s = sW[qq] * Ji[9];
+        for (int k = 0; k < 9; ++k) Fi[k] = d2f_rz(cof[k]) * idF;
+        const float s = sW[qq] * J[9];
         const float sa = s * (mu_c - lam_c * lnJ);
-        float4* o = reinterpret_cast<float4*>(pw + (size_t)w2 * C::PWF);
-        o[0] = bad ? make_float4(nan, nan, nan, nan) : make_float4(Mq[0], Mq[1], Mq[2], Mq[3]);
-        o[1] = bad ? make_float4(nan, nan, nan, nan) : make_float4(Mq[4], Mq[5], Mq[6], Mq[7]);
-        o[2] = bad ? make_float4(nan, nan, nan, 0.f) : make_float4(Mq[8], s, sa, 0.f);
+        float* rows = pw + e * C::PW_E + 12 * qq;  // M[c][k] = sum_I (F^-1)[I][c] (J^-1)[k][I]
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float mrow[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) mrow[k] = Fi[c] * J[3 * k] + Fi[3 + c] * J[3 * k + 1] + Fi[6 + c] * J[3 * k + 2];
+          *reinterpret_cast<float4*>(rows + 4 * c) =
+              bad ? make_float4(nan, nan, nan, nan) : make_float4(mrow[0], mrow[1], mrow[2], 0.f);
+        }
+        pws[e * C::Q + qq] = bad ? make_float2(nan, nan) : make_float2(s, sa);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->pw_full[slot]);
+      if (lane == 0) mbar_arrive(&bars->pw_full[gk]);
     }
     if (!ok) flag_error(err, ERR_TIMEOUT);
     // a prefetch issued before giving up (for iteration `it`) must land before the CTA leaves
-    if (kt == 0 && pending >= 0) mbar_wait(&bars->in_full[pending], (unsigned)((it >> 1) & 1));
+    if (kt == 0 && pending) mbar_wait_sleep(&bars->in_full[gk], (unsigned)((it >> 1) & 1));
   } else {
     // ----------------------------------------------------------- H builders
-    const int bt = tid - 32 * C::W_BLD;  // the H row (column of D) of this thread
-    const int e = bt / 9, cd = bt - 9 * (bt / 9), c = cd / 3, d = cd - 3 * (cd / 3);
-    const float dmu = c == d ? mu_c : 0.f;
-    char* hhi = sm + C::O_HHI + (size_t)(bt >> 3) * C::SBO + (size_t)(bt & 7) * 16;
-    char* hlo = sm + C::O_HLO + (size_t)(bt >> 3) * C::SBO + (size_t)(bt & 7) * 16;
+    const int gb = (warp - C::W_BLD) >> 2;                // half of the point groups
+    const int n = ((warp - C::W_BLD) & 3) * 32 + lane;   // H row = column of D
+    const int e = n / 9, cd = n - 9 * (n / 9), c = cd / 3, d = cd - 3 * (cd / 3);
+    char* hhi = sm + C::O_HHI + (size_t)(n >> 3) * C::SBO + (size_t)(n & 7) * 16;
+    char* hlo = sm + C::O_HLO + (size_t)(n >> 3) * C::SBO + (size_t)(n & 7) * 16;
+    static_assert(C::NG == 4, "two point groups per builder half");
     bool ok = true;
     int it = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
@@ -435,58 +525,21 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       unsigned w = 1;
       if (lane == 0) {
-        w = mbar_wait(&bars->pw_full[slot], (unsigned)((it >> 1) & 1));
-        if (w && it >= 1) w = mbar_wait(&bars->h_empty, (unsigned)((it - 1) & 1));
+        w = mbar_wait_sleep(&bars->pw_full[slot], (unsigned)((it >> 1) & 1));
+        if (w && it >= 1) w = mbar_wait_sleep(&bars->h_empty, (unsigned)((it - 1) & 1));
       }
       ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       if (!ok) break;
       if (e < ne) {
-        const float* pwe = reinterpret_cast<const float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT) + (size_t)e * C::Q * C::PWF;
-        const float* kp = reinterpret_cast<const float*>(sm + C::O_PWK) + slot * C::TE * 8 + 8 * e;
-        const float4 k0 = *reinterpret_cast<const float4*>(kp), k1 = *reinterpret_cast<const float4*>(kp + 4);
-        const float Km[9] = {k0.x, k0.w, k1.x, k0.w, k0.y, k1.y, k1.x, k1.y, k0.z};
-        for (int g = 0; g < C::NG; ++g) {
-          float h[72];
-#pragma unroll
-          for (int qi = 0; qi < 8; ++qi) {
-            const int qq = 8 * g + qi;
-            if (qq < C::Q) {
-              const float4 A0 = *reinterpret_cast<const float4*>(pwe + qq * C::PWF);
-              const float4 A1 = *reinterpret_cast<const float4*>(pwe + qq * C::PWF + 4);
-              const float4 A2 = *reinterpret_cast<const float4*>(pwe + qq * C::PWF + 8);
-              const float M[9] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w, A2.x};
-              const float s = A2.y, sa = A2.z;
-              const float sl = s * lam_c, smu = s * dmu;
-              float Mc[3], Md[3];
-#pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                Mc[k] = c == 0 ? M[k] : (c == 1 ? M[3 + k] : M[6 + k]);
-                Md[k] = d == 0 ? M[k] : (d == 1 ? M[3 + k] : M[6 + k]);
-              }
-#pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                const float pd = sa * Md[k], lc = sl * Mc[k];
-#pragma unroll
-                for (int l = 0; l < 3; ++l) h[9 * qi + 3 * k + l] = fmaf(pd, Mc[l], fmaf(lc, Md[l], smu * Km[3 * k + l]));
-              }
-            } else {
-#pragma unroll
-              for (int k = 0; k < 9; ++k) h[9 * qi + k] = 0.f;
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const int uidx = 9 * g + i;
-            if (uidx < C::KU) {
-              uint4 vh, vl;
-              split_bf16x2(h[8 * i], h[8 * i + 1], vh.x, vl.x);
-              split_bf16x2(h[8 * i + 2], h[8 * i + 3], vh.y, vl.y);
-              split_bf16x2(h[8 * i + 4], h[8 * i + 5], vh.z, vl.z);
-              split_bf16x2(h[8 * i + 6], h[8 * i + 7], vh.w, vl.w);
-              *reinterpret_cast<uint4*>(hhi + (size_t)uidx * C::LBO) = vh;
-              *reinterpret_cast<uint4*>(hlo + (size_t)uidx * C::LBO) = vl;
-            }
-          }
+        const float* pwe = reinterpret_cast<const float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT) + e * C::PW_E;
+        const float2* pws = reinterpret_cast<const float2*>(sm + C::O_PWS + (size_t)slot * C::PWS_SLOT) + e * C::Q;
+        const float* pwk = reinterpret_cast<const float*>(sm + C::O_PWK) + slot * C::TE * 12 + 12 * e;
+        if (gb == 0) {
+          nh_tc_build_group<P, 0>(pwe, pws, pwk, c, d, lam_c, hhi, hlo);
+          nh_tc_build_group<P, 1>(pwe, pws, pwk, c, d, lam_c, hhi, hlo);
+        } else {
+          nh_tc_build_group<P, 2>(pwe, pws, pwk, c, d, lam_c, hhi, hlo);
+          nh_tc_build_group<P, 3>(pwe, pws, pwk, c, d, lam_c, hhi, hlo);
         }
       }
       fence_proxy_async();

@@ -30,7 +30,7 @@ def ref_of(orc, form, p, coords, coeffs):
 
 def test_plan_selects_tensor_core_kernel(fea):
     pl = fea.plan(3, 2, precision=TC)
-    assert pl["tile"] == 14 and pl["threads"] == 416
+    assert pl["tile"] == 14 and pl["threads"] > 256 and pl["threads"] % 32 == 0
     # a tile other than the kernel's own is refused
     with pytest.raises(fea.FeaError) as e:
         fea.plan(3, 2, precision=TC, tile=8)
