@@ -71,6 +71,19 @@ __device__ __forceinline__ float d2f_rz(double x) {
   return __uint_as_float(e - 897u < 254u ? f : (e < 897u ? sign : 0x7fc00000u));
 }
 
+// Widening for values that come out of FTZ FP32 arithmetic (no subnormals):
+// exact for normal floats, zeros, infinities and NaN.  One 32 x 32 -> 64-bit
+// multiply-add places |x| << 29 across the two words with the exponent
+// rebias (1023 - 127) << 52 added; zero and inf/NaN are then patched.
+__device__ __forceinline__ double f2d_ftz(float f) {
+  const uint32_t u = __float_as_uint(f), a = u & 0x7fffffffu;
+  const uint64_t w = (uint64_t)a * (1ull << 29) + 0x3800000000000000ull;
+  uint32_t hi = (uint32_t)(w >> 32);
+  hi = a >= 0x7f800000u ? (hi | 0x7ff00000u) : hi;
+  hi = a == 0u ? 0u : hi;
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(uint32_t)w);
+}
+
 template <typename T> __device__ __forceinline__ T from_double(double x);
 template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f(x); }

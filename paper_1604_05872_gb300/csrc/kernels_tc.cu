@@ -54,27 +54,30 @@ static void nh_tc_table(std::vector<uint32_t>* words) {
   uint32_t* w = words->data();
   for (int q = 0; q < C::Q; ++q) w[L.offW + q] = fbits(t.W[q]);
   for (int i = 0; i < C::Q * C::NS * 3; ++i) w[L.offDphi + i] = fbits(t.dphi[i]);
-  // R_(a,b)[kk], kk = 9 q + 3 k + l: dPhi_a^k(X_q) dPhi_b^l(X_q) for q < Q, and for q = Q the
-  // point sum sum_q w_q dPhi_a^k(X_q) dPhi_b^l(X_q); split into BF16 hi and lo
+  // R_(a,b)[kk] = dPhi_a^k(X_q) dPhi_b^l(X_q) for q < Q, and for q = Q the point sum
+  // sum_q w_q dPhi_a^k(X_q) dPhi_b^l(X_q), at kk = kk_of(q, 3 k + l) (points interleaved in pairs);
+  // split into BF16 hi and lo
   auto g = [&](int q, int a, int k) { return t.dphi[((size_t)q * C::NS + a) * 3 + k]; };
   for (int pr = 0; pr < C::NPAIR; ++pr) {
     int a = 0, b = 0;
     sym_pair(pr, C::NS, &a, &b);
     uint32_t* hi = w + L.offR + (size_t)(2 * pr) * (C::K / 2);
     uint32_t* lo = hi + C::K / 2;
-    for (int kk = 0; kk < C::KK; ++kk) {
-      const int q = kk / 9, k = (kk % 9) / 3, l = kk % 3;
-      double r = 0.0;
-      if (q < C::Q) {
-        r = g(q, a, k) * g(q, b, l);
-      } else {
-        for (int p = 0; p < C::Q; ++p) r += t.W[p] * g(p, a, k) * g(p, b, l);
+    for (int q = 0; q <= C::Q; ++q) {
+      for (int kl = 0; kl < 9; ++kl) {
+        const int kk = C::kk_of(q, kl), k = kl / 3, l = kl % 3;
+        double r = 0.0;
+        if (q < C::Q) {
+          r = g(q, a, k) * g(q, b, l);
+        } else {
+          for (int p = 0; p < C::Q; ++p) r += t.W[p] * g(p, a, k) * g(p, b, l);
+        }
+        const uint16_t h = bf16_rn((float)r);
+        const uint16_t s = bf16_rn((float)(r - (double)bf16_val(h)));
+        const int sh = (kk & 1) ? 16 : 0;  // element 2j in the low half of column j
+        hi[kk >> 1] |= (uint32_t)h << sh;
+        lo[kk >> 1] |= (uint32_t)s << sh;
       }
-      const uint16_t h = bf16_rn((float)r);
-      const uint16_t s = bf16_rn((float)(r - (double)bf16_val(h)));
-      const int sh = (kk & 1) ? 16 : 0;  // element 2j in the low half of column j
-      hi[kk >> 1] |= (uint32_t)h << sh;
-      lo[kk >> 1] |= (uint32_t)s << sh;
     }
   }
 }
