@@ -52,6 +52,7 @@
 // tensor memory and leaves.
 #pragma once
 #include "common.cuh"
+#include "launch.cuh"
 #include "log_f64.cuh"
 #include "mbar.cuh"
 #include "tc.cuh"
@@ -120,6 +121,9 @@ struct NhTc {
   static_assert(O_PW % 16 == 0 && (PW_E * 4) % 16 == 0 && O_PWK % 16 == 0 && O_UT % 16 == 0 && O_DPHI % 16 == 0,
                 "vector alignment");
   static_assert(CLEN <= 32 && NS * 3 <= 32, "padded rows");
+  static_assert(NS % 2 == 0, "node pairs");
+  // rows of u and of dPhi at a point hold the nodes in pairs: entry 6 (a / 2) + 2 i + a % 2
+  FEA_HD static constexpr int node_slot(int a, int i) { return 6 * (a >> 1) + 2 * i + (a & 1); }
 
   FEA_HD static int max_tile() { return TE; }
   FEA_HD static int pref_tile() { return TE; }
@@ -290,7 +294,12 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
   for (int i = tid; i < C::Q; i += C::NTH) sW[i] = tab[L.offW + i];
   for (int i = tid; i < C::Q * C::RS; i += C::NTH) {
     const int qq = i / C::RS, j = i - qq * C::RS;
-    sD[i] = j < C::NS * 3 ? tab[L.offDphi + qq * C::NS * 3 + j] : 0.f;
+    if (j >= C::NS * 3) sD[i] = 0.f;
+  }
+  __syncthreads();
+  for (int i = tid; i < C::Q * C::NS * 3; i += C::NTH) {  // dPhi_a^k at node_slot(a, k)
+    const int qq = i / (C::NS * 3), r = i - qq * (C::NS * 3);
+    sD[qq * C::RS + C::node_slot(r / 3, r % 3)] = tab[L.offDphi + i];
   }
   {
     uint4* z = reinterpret_cast<uint4*>(sm);
@@ -404,7 +413,8 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       float* geo = reinterpret_cast<float*>(sm + C::O_GEO) + gb * C::TE * 24;
       for (int i = gt; i < ne * C::CLEN; i += NG_T) {
         const int e = i / C::CLEN;
-        ut[e * C::RU + (i - e * C::CLEN)] = d2f_rz(us[i]);  // displacement DOFs for the FP32 grad u
+        const int r = i - e * C::CLEN;  // displacement DOF u_a[c] at 3 a + c, to its node-pair slot
+        ut[e * C::RU + C::node_slot(r / 3, r % 3)] = d2f_rz(us[i]);
       }
       if (gt < ne) {  // FP64 geometry of element gt
         double adj[9];
@@ -505,32 +515,32 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       }
       for (int w2 = kt; w2 < ne * C::Q; w2 += 128) {
         const int e = w2 / C::Q, qq = w2 - e * C::Q;
-        float uv[32];  // u_a[i] at 3 a + i
+        float uv[32], dv[32];  // u_a[i] and dPhi_a^k at node_slot(a, i or k)
         {
           const float4* u4 = reinterpret_cast<const float4*>(ut + C::RU * e);
+          const float4* d4 = reinterpret_cast<const float4*>(sD + C::RS * qq);
 #pragma unroll
           for (int v = 0; v < 8; ++v) {
-            const float4 uu = u4[v];
+            const float4 uu = u4[v], dd = d4[v];
             uv[4 * v] = uu.x; uv[4 * v + 1] = uu.y; uv[4 * v + 2] = uu.z; uv[4 * v + 3] = uu.w;
+            dv[4 * v] = dd.x; dv[4 * v + 1] = dd.y; dv[4 * v + 2] = dd.z; dv[4 * v + 3] = dd.w;
           }
         }
-        float gr[9];  // gr[3 i + k] = sum_a u_a[i] dPhi_a^k
+        // gr[3 i + k] = sum_a u_a[i] dPhi_a^k, two nodes at a time (packed), even and odd nodes summed last
+        float2 acc[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) gr[k] = 0.f;
-        const float4* d4 = reinterpret_cast<const float4*>(sD + C::RS * qq);
+        for (int k = 0; k < 9; ++k) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const float4 dd = d4[v];
-          const float dv[4] = {dd.x, dd.y, dd.z, dd.w};
+        for (int np = 0; np < C::NS / 2; ++np)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int r = 4 * v + j;  // dPhi_a^k with a = r / 3, k = r % 3
-            if (r < C::NS * 3) {
+          for (int i = 0; i < 3; ++i)
 #pragma unroll
-              for (int i = 0; i < 3; ++i) gr[3 * i + r % 3] = fmaf(uv[3 * (r / 3) + i], dv[j], gr[3 * i + r % 3]);
-            }
-          }
-        }
+            for (int k = 0; k < 3; ++k)
+              acc[3 * i + k] = __ffma2_rn(make_float2(uv[6 * np + 2 * i], uv[6 * np + 2 * i + 1]),
+                                          make_float2(dv[6 * np + 2 * k], dv[6 * np + 2 * k + 1]), acc[3 * i + k]);
+        float gr[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) gr[k] = acc[k].x + acc[k].y;
         float J[12];
         {
           const float4* j4 = reinterpret_cast<const float4*>(geo + 24 * e);
@@ -564,13 +574,13 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
         if (bad) flag_error(err, ERR_DEGENERATE);
         // the cancellation-prone cofactors, det F and ln det F are FP64; F^-1 = cof / det F
         // is a well-conditioned scaling done after rounding to FP32
-        const float idF = __frcp_rn(d2f_rz(dF));
+        // H = alpha M'_d M'_c + lam M'_c M'_d with M' = sqrt(s) M: sqrt(s) rides on 1 / det F
+        const float rs = __fsqrt_rn(sW[qq] * J[9]);
+        const float idF = __frcp_rn(d2f_rz(dF)) * rs;
         const float lnJ = d2f_rz(log_f64(dF));
-        float Fi[9];  // Fi[3 I + c] = (F^-1)[I][c]
+        float Fi[9];  // Fi[3 I + c] = sqrt(s) (F^-1)[I][c]
 #pragma unroll
         for (int k = 0; k < 9; ++k) Fi[k] = d2f_rz(cof[k]) * idF;
-        const float s = sW[qq] * J[9];
-        const float rs = __fsqrt_rn(s);  // H = alpha M'_d M'_c + lam M'_c M'_d with M' = sqrt(s) M
         const float al = mu_c - lam_c * lnJ;
         float* rec = pw + e * C::PW_E + 20 * (qq >> 1) + (qq & 1);  // this point's slots of its pair record
         rec[0] = bad ? nan : al;
@@ -578,7 +588,7 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int k = 0; k < 3; ++k)  // M[c][k] = sum_I (F^-1)[I][c] (J^-1)[k][I]
-            rec[2 + 6 * c + 2 * k] = bad ? nan : rs * (Fi[c] * J[3 * k] + Fi[3 + c] * J[3 * k + 1] + Fi[6 + c] * J[3 * k + 2]);
+            rec[2 + 6 * c + 2 * k] = bad ? nan : Fi[c] * J[3 * k] + Fi[3 + c] * J[3 * k + 1] + Fi[6 + c] * J[3 * k + 2];
       }
       __syncwarp();
       if (lane == 0) {
