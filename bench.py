@@ -53,6 +53,9 @@ PROFILES = {
     "neohookean_p2_500k": ("neohookean_p2_se_500k.md",
                            ["common.cuh", "layout.h", "launch.cuh", "se_vec.cuh", "sym.cuh", "log_f64.cuh",
                             "log_table.h", "planner.cpp"]),
+    "neohookean_p2_500k@bf16x2": ("neohookean_p2_tc_500k.md",
+                                  ["common.cuh", "layout.h", "launch.cuh", "mbar.cuh", "tc.cuh", "nh_tc.cuh",
+                                   "log_f64.cuh", "log_table.h", "kernels_tc.cu"]),
     "helmholtz_p2_global_1M": ("global_helmholtz_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh", "planner.cpp"]),
     "helmholtz_load_p2_1M": ("helmholtz_load_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh"]),
     "neohookean_residual_p2_500k": ("neohookean_residual_p2_500k.md",
@@ -254,8 +257,37 @@ def fp64_ops_per_element(form, p, variant, Q):
 
 # FP64 lane-instructions per Neo-Hookean point: F = I + grad u (3 additions), the
 # cofactors of F (18) and det F (3), two tests of det F, and ln det F by the
-# table-driven logarithm (13)
+# table-driven logarithm (13); the tensor-core kernel tests det F with integer ops
 NEO_POINT_FP64 = 3 + 18 + 3 + 2 + 13
+NEO_POINT_FP64_TC = 3 + 18 + 3 + 13
+
+
+def precision_of(args, fea, form, p):
+    """(precision code, name, uses the tensor-core kernel) for a (form, degree)."""
+    names = {"fp32": fea.PREC_FP32, "bf16x2": fea.PREC_BF16X2, "fp64": fea.PREC_FP64}
+    tc = fea.plan(form, p, precision=fea.PREC_BF16X2)["threads"] != 256
+    if args.precision == "auto":
+        return (fea.PREC_BF16X2, "bf16x2", True) if tc else (fea.PREC_FP32, "fp32", False)
+    prec = names[args.precision]
+    return prec, args.precision, tc and prec == fea.PREC_BF16X2
+
+
+def tc_flops_per_element(form, p):
+    """Useful tensor-core flops per element of the split-BF16 Neo-Hookean kernel:
+    rows = 2 x the symmetric basis pairs (hi and lo parts of the reference
+    tables), 9 columns (c, d) per element, K = 9 (Q + 1) (the points and the
+    point-summed term), two passes (hi and lo parts of H), 2 flops per MAC."""
+    ns = (p + 1) * (p + 2) * (p + 3) // 6
+    Q = (p + 1) ** 3
+    return 2 * 2 * (ns * (ns + 1)) * 9 * 9 * (Q + 1)
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 def main():
@@ -271,6 +303,9 @@ def main():
     ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_1604_05872_gb300", "data", "tuning_gb300.json"),
                     help="tuning JSON (records + MLP) for the stream workload ('' for the flop-count choice only)")
     ap.add_argument("--out-f32", action="store_true", help="FP32 output (element matrices stored as float)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x2", "fp64"],
+                    help="contraction arithmetic; auto = split-BF16 tensor cores where a tensor-core kernel exists "
+                         "(Neo-Hookean P2), FP32 elsewhere")
     ap.add_argument("--clocks-log", default="", help="also log nvidia-smi clocks of the timed regions to this CSV")
     args = ap.parse_args()
     global CLOCKS_LOG
@@ -329,11 +364,12 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     n = out.shape[1]
     esz = 4 if f32 else 8
     stream = torch.cuda.current_stream()
-    pl = fea.plan(form, p)
+    prec, prec_name, tc = precision_of(args, fea, form, p)
+    pl = fea.plan(form, p, precision=prec)
     bytes_elem = 96 + 8 * fea.coeff_len(form, p) + esz * n * n
 
     for _ in range(args.warmup):
-        fea.assemble(form, p, c, fc, out=out, out_f32=f32)
+        fea.assemble(form, p, c, fc, out=out, out_f32=f32, precision=prec)
     fea.sync()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -343,7 +379,7 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         with ClockSampler(local) as clk:
             ev0.record(stream)
             for _ in range(args.steps):
-                fea.assemble(form, p, c, fc, out=out, out_f32=f32)
+                fea.assemble(form, p, c, fc, out=out, out_f32=f32, precision=prec)
             ev1.record(stream)
             barrier()
         ms = ev0.elapsed_time(ev1) / args.steps
@@ -356,7 +392,7 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
             for a, b in evs:
                 flush.fill_(1.0)
                 a.record(stream)
-                fea.assemble(form, p, c, fc, out=out, out_f32=f32)
+                fea.assemble(form, p, c, fc, out=out, out_f32=f32, precision=prec)
                 b.record(stream)
             torch.cuda.synchronize()
             barrier()
@@ -387,25 +423,29 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     del out64
     ho = torch.empty((E, n, n), dtype=torch.float32 if f32 else torch.float64).pin_memory()
     for _ in range(2):
-        fea.assemble_host(form, p, hc, hf, ho, out_f32=f32)
+        fea.assemble_host(form, p, hc, hf, ho, out_f32=f32, precision=prec)
     barrier()
     e2e_steps = max(3, args.steps // 4)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fea.assemble_host(form, p, hc, hf, ho, out_f32=f32)
+        fea.assemble_host(form, p, hc, hf, ho, out_f32=f32, precision=prec)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) / e2e_steps * 1e3)
 
     hbm, peak_kind = peaks()
     alg_bytes = E * bytes_elem
-    flops = E * pl["flops_run"]
-    f64 = E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"])
+    flops = E * (tc_flops_per_element(form, p) if tc else pl["flops_run"])
+    f64 = E * (30 + NEO_POINT_FP64_TC * pl["quad_points"] if tc else fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]))
     t_hbm = alg_bytes / (hbm * 1e9)
-    t_f32 = flops / (FP32_PEAK_TFLOPS * 1e12)
+    bf16, bf16_kind = bf16_peak()
+    t_f32 = flops / ((bf16 if tc else FP32_PEAK_TFLOPS) * 1e12)
     t_f64 = f64 / (FP64_PEAK_TINSTR * 1e12)
     if t_hbm >= max(t_f32, t_f64):
         roof = {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_kind": peak_kind}
+    elif t_f32 >= t_f64 and tc:
+        roof = {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "peak_kind": bf16_kind + " bf16 dense (split-BF16 products)"}
     elif t_f32 >= t_f64:
         roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_kind": "derived: FP32 lanes x clock"}
@@ -413,19 +453,25 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         roof = {"bound": "alu", "achieved": f64 / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TINSTR,
                 "unit": "T FP64 lane-instructions/s", "peak_kind": "derived: FP64 lanes x clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = profiled_traffic(args.workload) if E == E0 and not f32 else None
+    roof["traffic"] = profiled_traffic(args.workload + ("@bf16x2" if tc else "")) if E == E0 and not f32 else None
     roof["alg_bytes_per_launch"] = alg_bytes
-    roof["bound_times_ms"] = {"hbm": t_hbm * 1e3, "fp32": t_f32 * 1e3, "fp64": t_f64 * 1e3}
+    roof["bound_times_ms"] = {"hbm": t_hbm * 1e3, ("tensor" if tc else "fp32"): t_f32 * 1e3, "fp64": t_f64 * 1e3}
+    if tc:
+        roof["tensor_achieved_tflops"] = flops / (ms * 1e-3) / 1e12
+        roof["tensor_frac"] = roof["tensor_achieved_tflops"] / bf16
     cfg = {"workload": args.workload, "form": ["mass", "helmholtz", "elasticity", "neohookean"][form],
            "degree": p, "elements": E, "quad_points": pl["quad_points"], "local_matrix": "%dx%d %s" % (n, n, "f32" if f32 else "f64"),
-           "variant": fea.VARIANT_NAMES[pl["variant"]], "tile": pl["tile"], "geometry": "f64",
-           "contraction": "f32", "parallelism": "dp%d (element shards)" % world,
+           "variant": fea.VARIANT_NAMES[pl["variant"]] + (" (per-point pre-evaluation on tcgen05)" if tc else ""),
+           "tile": pl["tile"], "geometry": "f64",
+           "contraction": "bf16x2 split operands on tcgen05 tensor cores, f32 accumulation" if tc else prec_name,
+           "parallelism": "dp%d (element shards)" % world,
            "l2": "inputs+outputs %.0f MB per step%s" % (alg_bytes / 1e6, " > 129 MB L2; no flush" if not small
                                                          else " (fits L2): L2 flushed before every step, per-step events")}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
+        "vs_baseline": None, "dtype": "bf16x2" if tc else prec_name.replace("fp", "f"), "data": "synthetic",
+        "config": cfg, "roofline": roof,
         "comparator": {"kernel": "plain FP64 quadrature nest", "value": naive_rate, "unit": METRIC,
                        "elements": En, "ms_per_step": ms_naive, "speedup": value / world / naive_rate},
         "e2e": {"value": E * world / (e2e_ms * 1e-3), "unit": METRIC,
@@ -640,26 +686,35 @@ def run_stream(args, fea, torch, barrier, max_over_ranks, world, local):
         built.append((form, p, c, f, fea.empty_out(form, p, E)))
         total += E
 
+    bf16, _ = bf16_peak()
+    prec_name = "bf16x2" if args.precision in ("auto", "bf16x2") else "fp32"
+    prec = fea.PREC_BF16X2 if prec_name == "bf16x2" else fea.PREC_FP32
+
     def bound_time():
         tb, byt = 0.0, 0
         for form, p, c, f, o in built:
-            pl = fea.plan(form, p)
+            pl = fea.plan(form, p, precision=prec)
+            tc = pl["threads"] != 256
             E = c.shape[0]
             b = E * pl["bytes"]
             byt += b
-            tb += max(b / (hbm * 1e9), E * pl["flops_run"] / (FP32_PEAK_TFLOPS * 1e12),
-                      E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]) / (FP64_PEAK_TINSTR * 1e12))
+            if tc:
+                tb += max(b / (hbm * 1e9), E * tc_flops_per_element(form, p) / (bf16 * 1e12),
+                          E * (30 + NEO_POINT_FP64_TC * pl["quad_points"]) / (FP64_PEAK_TINSTR * 1e12))
+            else:
+                tb += max(b / (hbm * 1e9), E * pl["flops_run"] / (FP32_PEAK_TFLOPS * 1e12),
+                          E * fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]) / (FP64_PEAK_TINSTR * 1e12))
         return tb, byt
 
     def timed(steps, fused=False):
         for _ in range(args.warmup):
-            fea.assemble_batch(built, fused=fused)
+            fea.assemble_batch(built, fused=fused, precision=fea.PREC_FP32 if fused else prec)
         fea.sync()
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
         for _ in range(steps):
-            fea.assemble_batch(built, fused=fused)
+            fea.assemble_batch(built, fused=fused, precision=fea.PREC_FP32 if fused else prec)
         ev1.record()
         barrier()
         fea.sync()
@@ -691,6 +746,8 @@ def run_stream(args, fea, torch, barrier, max_over_ranks, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "stream_64req_2M", "requests": len(reqs), "elements": total, "choice": choice,
+                   "contraction": prec_name + (" (split-BF16 tensor cores for the Neo-Hookean P2 requests, FP32 elsewhere)"
+                                               if prec_name == "bf16x2" else ""),
                    "launch": "one replayed CUDA graph per step: each request's persistent kernel, 4 concurrent branches"},
         "roofline": {"bound": "mixed", "achieved": t_bound * 1e3, "peak": ms, "unit": "ms (sum of per-request bound times / measured)",
                      "frac": t_bound * 1e3 / ms, "traffic": None, "alg_bytes_per_launch": alg_bytes,

@@ -3,6 +3,7 @@
 Tolerances (per-element relative Frobenius error, max over elements):
   FP64 path (plain and flop-reduced)  <= 1e-12
   FP32 contraction, FP64 geometry     <= 1e-5
+  split-BF16 tensor-core contraction  <= 1e-5 (Neo-Hookean P2; the other forms run FP32 in that mode)
 Sizes span several tiles and end in a ragged tail; the full benchmark sizes are
 checked on sampled elements in test_fullsize_gpu.py.
 """
@@ -14,7 +15,7 @@ from paper_1604_05872_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-12, 1: 1e-5}
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-5}
 FORMS = [0, 1, 2, 3]
 DEGREES = [1, 2, 3, 4]
 
@@ -43,7 +44,7 @@ def variants(form):
     return [1, 2] if form != 3 else [1]
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 @pytest.mark.parametrize("p", DEGREES)
 @pytest.mark.parametrize("form", FORMS)
 def test_flop_reduced_variants_match_oracle(fea, orc, form, p, prec):

@@ -35,18 +35,19 @@ def _rows(out, idx):
     return out.index_select(0, torch.from_numpy(idx).to(out.device)).cpu().numpy()
 
 
-@pytest.mark.parametrize("name,form,p,E,aniso", [
-    ("helmholtz_p2_1M", 1, 2, 1_000_000, False),
-    ("mass_p1_10k", 0, 1, 10_000, False),
-    ("elasticity_p3_200k", 2, 3, 200_000, True),
-    ("neohookean_p2_500k", 3, 2, 500_000, False),
+@pytest.mark.parametrize("name,form,p,E,aniso,prec", [
+    ("helmholtz_p2_1M", 1, 2, 1_000_000, False, 1),
+    ("mass_p1_10k", 0, 1, 10_000, False, 1),
+    ("elasticity_p3_200k", 2, 3, 200_000, True, 1),
+    ("neohookean_p2_500k", 3, 2, 500_000, False, 1),
+    ("neohookean_p2_500k", 3, 2, 500_000, False, 2),  # split-BF16 tensor cores, as bench.py runs it
 ])
-def test_benchmark_workload_full_size(fea, orc, name, form, p, E, aniso):
+def test_benchmark_workload_full_size(fea, orc, name, form, p, E, aniso, prec):
     import torch
     coords, coeffs = inputs.workload(form, p, E, seed=inputs.SEED, anisotropic=aniso)
     c = torch.from_numpy(coords).cuda()
     f = None if form == 0 else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
-    out = fea.assemble(form, p, c, f)
+    out = fea.assemble(form, p, c, f, precision=prec)
     fea.sync()
     idx = np.arange(E) if E <= 10_000 else _sample(coords, 1500, seed=E)
     got = _rows(out, idx)
@@ -62,8 +63,8 @@ def test_benchmark_workload_full_size(fea, orc, name, form, p, E, aniso):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("fused", [False, True])
-def test_stream_64_requests_full_size(fea, orc, fused):
+@pytest.mark.parametrize("fused,prec", [(False, 1), (True, 1), (False, 2)])
+def test_stream_64_requests_full_size(fea, orc, fused, prec):
     """The 2M-element, 64-request stream exactly as bench.py builds it."""
     import torch
     reqs = inputs.stream_requests()
@@ -74,7 +75,7 @@ def test_stream_64_requests_full_size(fea, orc, fused):
         f = None if form == 0 else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
         built.append((form, p, c, f, fea.empty_out(form, p, E)))
         host.append((coords, coeffs))
-    fea.assemble_batch(built, fused=fused)
+    fea.assemble_batch(built, fused=fused, precision=prec)
     fea.sync()
     worst = 0.0
     for k, ((form, p, c, f, o), (coords, coeffs)) in enumerate(zip(built, host)):
