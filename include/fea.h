@@ -239,21 +239,22 @@ int fea_assemble_batch(const fea_request* reqs, int nreq, const fea_options* opt
 int fea_assemble_batch_fused(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
 
 /* The batched launch above, for callers that cannot allocate device memory at
- * the moment they assemble: code that runs while a CUDA graph is being
- * captured (an allocation would break the capture), code living inside
- * another framework's memory pool that forbids allocations outside it, and
- * latency-critical loops where an allocation may block or fail.  The paper has
- * no counterpart.  The work-list counter and the request list live in a
- * file-scope device array of the library (256 B + 512 request slots, about
+ * the moment they assemble: code that lives inside another framework's memory
+ * pool and may not allocate outside it, or a latency-critical loop where an
+ * allocation may block, fail or cost more than the assembly itself.  The
+ * paper has no counterpart.  The work-list counter and the request list live in
+ * a file-scope device array of the library (256 B + 512 request slots, about
  * 37 KB, held by every GPU that loads the library until exit) instead of
- * allocations, and the kernel is launched directly on `stream`.  Limits: at
- * most 512 requests per call (FEA_EINVAL beyond); the library's state and the
- * tables of each requested (form, degree) must already exist on the current
- * device -- any earlier allocating call there makes them -- else FEA_EINVAL.
- * The first call on a device looks up the array's device address; make it
- * before any stream capture.  All calls share the array and each resets its
- * counter, so calls whose kernels overlap on the GPU race: keep them ordered
- * (one stream). */
+ * allocations; the request list reaches it as kernel parameters of a small
+ * copy kernel, and the batched kernel is launched directly on `stream`.  The
+ * call allocates nothing, on the device or on the host.  Limits: at most 512
+ * requests per call (FEA_EINVAL beyond); FP32 contraction only; the library's
+ * state and the tables of each requested (form, degree) must already exist on
+ * the current device -- any earlier allocating call there makes them -- else
+ * FEA_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All
+ * calls share the array and each restarts its counter at zero, so calls whose
+ * kernels overlap on the GPU race: keep them ordered (one stream). */
 int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_options* opt, void* stream);
 
 /* Wait for `stream`, then report (and clear) the device error word. */

@@ -125,12 +125,35 @@ int get_dev_state(DevState** out);
 BatchState*& dev_batch(DevState* st);
 unsigned* device_error_word(DevState* st);
 int device_sms(DevState* st);
+size_t device_smem_optin(DevState* st);
+int device_index(DevState* st);
 const void* table_ptr(DevState* st, int form, int p, int prec, int* rc);
 int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch);
 int set_error(int code, const char* msg);
 int check_device_ptr(const void* p, const char* what, bool allow_null);
 int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, const double* coords,
                    const double* coeffs, void* out, int out_f32, PreparedLaunch* L);
+
+// The batched kernel's dynamic shared-memory ceiling, raised once per device to
+// the device limit (a ceiling only permits; each launch asks for its own
+// size), so that no launch path lowers it under another path's cached graph.
+static int batch_kernel_smem_ceiling(DevState* st) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  const int dev = device_index(st);
+  if (dev < 0 || dev >= 64) return set_error(FEA_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return FEA_OK;
+  const void* fn = reinterpret_cast<const void*>(&batch_kernel);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)device_smem_optin(st) - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  done[dev] = true;
+  return FEA_OK;
+}
 
 static bool same_sig(const std::vector<Req>& a, const std::vector<Req>& b) {
   if (a.size() != b.size()) return false;
@@ -201,8 +224,7 @@ int batch_fused_impl(const fea_request* reqs, int nreq, const fea_options* opt, 
     if ((e = cudaMemcpy(bs->dreqs, R.data(), R.size() * sizeof(Req), cudaMemcpyHostToDevice)) != cudaSuccess)
       return set_error(FEA_ECUDA, cudaGetErrorString(e));
     const void* fn = reinterpret_cast<const void*>(&batch_kernel);
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return set_error(FEA_ECUDA, cudaGetErrorString(e));
+    if ((rc = batch_kernel_smem_ceiling(st))) return rc;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem)) != cudaSuccess || per_sm < 1)
       return set_error(FEA_ECUDA, "batch kernel occupancy");
@@ -335,12 +357,13 @@ int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* 
 // The batched launch without any device allocation.
 //
 // Some callers cannot call cudaMalloc at the moment they assemble: code that
-// runs while a CUDA graph is being captured, code inside another framework's
-// memory pool that forbids allocations outside the pool, or latency-critical
-// loops where an allocation could block.  fea_assemble_batch_noalloc serves
-// them: the work-list counter and the request list that the batched kernel
-// needs live in the file-scope device array below instead of library
-// allocations, and the launch is made directly (no graph).  Limits: at most
+// lives inside another framework's memory pool and may not allocate outside
+// it, or a latency-critical loop where an allocation may block, fail or cost
+// more than the assembly.  fea_assemble_batch_noalloc serves them: the
+// work-list counter and the request list that the batched kernel needs sit in
+// the file-scope device array below instead of in library allocations; the
+// request list is handed over as kernel parameters (by value) to a small copy
+// kernel, and the batched kernel is launched directly.  Limits: at most
 // kNoAllocMaxRequests requests per call; the device state and the tables of
 // every (form, degree) in the batch must already exist on the current device
 // (made by any earlier allocating call there), otherwise the call is
@@ -359,7 +382,21 @@ namespace {
 constexpr int kMaxDevices = 64;
 unsigned char* g_noalloc_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
 std::mutex g_noalloc_mu;
+
+// Requests handed to the copy kernel by value, a few dozen at a time (well
+// inside the kernel-parameter limit).
+constexpr int kUploadChunk = 48;
+struct ReqChunk {
+  Req r[kUploadChunk];
+};
 }  // namespace
+
+// dst[0 .. n) = chunk; the first chunk also restarts the work-list counter (the
+// array keeps the previous call's contents).
+__global__ void noalloc_upload(ReqChunk chunk, int n, Req* dst, unsigned long long* counter, int reset) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = chunk.r[i];
+  if (reset && threadIdx.x == 0) *counter = 0ull;
+}
 
 int batch_noalloc_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   if (nreq < 0 || (nreq > 0 && !reqs)) return set_error(FEA_EINVAL, "bad request list");
@@ -388,8 +425,20 @@ int batch_noalloc_impl(const fea_request* reqs, int nreq, const fea_options* opt
     }
     scratch = g_noalloc_ptr[dev];
   }
-  Req R[kNoAllocMaxRequests];
-  int nr = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(scratch);
+  Req* dr = reinterpret_cast<Req*>(scratch + kNoAllocReqOffset);
+  // requests go to the device array a chunk at a time, as kernel parameters of the copy kernel
+  ReqChunk chunk;
+  int nc = 0;   // requests in `chunk`
+  int nr = 0;   // requests uploaded or in `chunk`
+  auto flush = [&]() -> int {
+    if (nc == 0) return FEA_OK;
+    noalloc_upload<<<1, 64, 0, s>>>(chunk, nc, dr + (nr - nc), ctr, nr == nc ? 1 : 0);
+    const cudaError_t ce = cudaGetLastError();
+    nc = 0;
+    return ce == cudaSuccess ? FEA_OK : set_error(FEA_ECUDA, cudaGetErrorString(ce));
+  };
   size_t smem = 0;
   long long tiles = 0;
   int rc;
@@ -406,7 +455,8 @@ int batch_noalloc_impl(const fea_request* reqs, int nreq, const fea_options* opt
     if (pl.variant == FEA_VARIANT_NAIVE) return set_error(FEA_EINVAL, "the batched launch has no plain variant");
     const void* tab = existing_table(st, r.form, r.degree, 1);
     if (!tab) return set_error(FEA_EINVAL, "tables of a requested form/degree are not resident: make one allocating call first");
-    Req& q = R[nr++];
+    Req& q = chunk.r[nc++];
+    ++nr;
     std::memset(&q, 0, sizeof(q));
     q.coords = r.coords;
     q.coeffs = r.coeffs;
@@ -422,22 +472,15 @@ int batch_noalloc_impl(const fea_request* reqs, int nreq, const fea_options* opt
     q.tile0 = tiles;
     tiles += (r.E + pl.tile - 1) / pl.tile;
     smem = std::max(smem, pl.smem);
+    if (nc == kUploadChunk && (rc = flush())) return rc;
   }
   if (nr == 0) return FEA_OK;
-  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = flush())) return rc;
   const void* fn = reinterpret_cast<const void*>(&batch_kernel);
-  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return set_error(FEA_ECUDA, cudaGetErrorString(e));
+  if ((rc = batch_kernel_smem_ceiling(st))) return rc;
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem)) != cudaSuccess || per_sm < 1)
     return set_error(FEA_ECUDA, "batch kernel occupancy");
-  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(scratch);
-  Req* dr = reinterpret_cast<Req*>(scratch + kNoAllocReqOffset);
-  // the array keeps the previous call's contents: the counter must restart at zero
-  if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s)) != cudaSuccess)
-    return set_error(FEA_ECUDA, cudaGetErrorString(e));
-  if ((e = cudaMemcpyAsync(dr, R, (size_t)nr * sizeof(Req), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return set_error(FEA_ECUDA, cudaGetErrorString(e));
   const int grid = (int)std::min<long long>(tiles, (long long)device_sms(st) * per_sm);
   unsigned* err = device_error_word(st);
   long long total = tiles;

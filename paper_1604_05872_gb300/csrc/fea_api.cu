@@ -78,6 +78,8 @@ static int get_dev(DevState** out) {
 
 unsigned* device_error_word(DevState* st) { return st->err; }
 int device_sms(DevState* st) { return st->sms; }
+size_t device_smem_optin(DevState* st) { return st->smem_optin; }
+int device_index(DevState* st) { return st->dev; }
 int get_dev_state(DevState** out) { return get_dev(out); }
 BatchState*& dev_batch(DevState* st) { return st->batch; }
 int set_error(int code, const char* msg) { return fail(code, msg); }
