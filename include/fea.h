@@ -260,6 +260,18 @@ int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_opti
 /* Wait for `stream`, then report (and clear) the device error word. */
 int fea_sync(void* stream);
 
+/* Fault injection for tests of the failure path (the paper has no
+ * counterpart): the next standalone launch skips the input copy of its global
+ * tile `tile` (-1 clears; other values below -1 give FEA_EINVAL).  The kernels
+ * that stream their inputs by bulk copies (mass and Helmholtz P1-P3 FP32, the
+ * one-pass global assembly, the split-BF16 Neo-Hookean kernel) honour it: the
+ * CTA that runs that tile waits for inputs that never arrive, its bounded wait
+ * gives up (after a few seconds), the CTA leaves after its copies in flight have
+ * landed, the outputs of that tile and of that CTA's later tiles are left
+ * unwritten, and the next fea_sync returns FEA_ETIMEOUT.  Other kernels ignore
+ * it.  The setting applies to one launch and then clears itself. */
+int fea_test_skip_input_copy(int64_t tile);
+
 /* Plan for (form, degree, options) without launching anything. */
 int fea_plan(int form, int degree, const fea_options* opt, fea_plan_info* info);
 

@@ -27,7 +27,7 @@ EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points
            "fea_csr_scatter_map", "fea_scatter_add_csr_mapped", "fea_assemble_csr", "fea_log_f64",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_fused",
            "fea_assemble_batch_noalloc",
-           "fea_sync", "fea_plan", "fea_plan_flop",
+           "fea_sync", "fea_test_skip_input_copy", "fea_plan", "fea_plan_flop",
            "fea_op_count", "fea_opcount_program", "fea_sharing_elimination", "fea_vertex_cover",
            "fea_increase_factor", "fea_num_monomials", "fea_theta", "fea_algorithm3",
            "fea_tune_set", "fea_tune_clear", "fea_mlp_num_params", "fea_mlp_scratch_floats",
@@ -91,6 +91,7 @@ def load(path=None):
     lib.fea_scatter_add_csr_mapped.argtypes = [i64, i, vp, i, vp, i, i64, vp, vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
+    lib.fea_test_skip_input_copy.argtypes = [i64]
     lib.fea_plan.argtypes = [i, i, P(Options), P(PlanInfo)]
     lib.fea_plan_flop.argtypes = [i, i, P(Options), P(PlanInfo)]
     lib.fea_op_count.argtypes = [i, i, i, P(i64), P(i64)]
@@ -309,6 +310,12 @@ def assemble_batch_noalloc(requests, out_f32=False, stream=None):
                          None if coeffs is None else coeffs.data_ptr(), out.data_ptr())
     o = options(PREC_FP32, out_f32)
     _check(load().fea_assemble_batch_noalloc(arr, len(requests), ctypes.byref(o), _stream_ptr(stream)))
+
+
+def skip_input_copy_once(tile):
+    """Fault injection for tests: the next standalone launch skips the input copy of global tile
+    `tile` (-1 clears); its bounded wait runs out and the next sync raises FeaError(ETIMEOUT)."""
+    _check(load().fea_test_skip_input_copy(tile))
 
 
 def sync(stream=None):

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,8 @@ bool tc_table_words(int form, int p, std::vector<uint32_t>* words);
 const KernelInfo* find_tc_kernel(int form, int p);
 
 static thread_local std::string g_last_error;
+// test hook (fea_test_skip_input_copy): 1 + the tile whose input copy the next launch skips
+static std::atomic<int64_t> g_skip_copy{0};
 static int fail(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
@@ -283,6 +286,7 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
   q.out_f32 = out_f32;
   q.kind = 0;
   q.tile0 = 0;
+  q.skip_copy = g_skip_copy.exchange(0);  // test hook, one launch only
   const int64_t ntiles = (E + tile - 1) / tile;
   int per_sm = 0;
   {
@@ -601,6 +605,11 @@ int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_opti
   return batch_noalloc_impl(reqs, nreq, opt, stream);
 }
 int fea_sync(void* stream) { return sync_impl(stream); }
+int fea_test_skip_input_copy(int64_t tile) {
+  if (tile < -1) return fail(FEA_EINVAL, "tile must be >= -1");
+  g_skip_copy.store(tile + 1);
+  return FEA_OK;
+}
 
 static int plan_impl(int form, int degree, const fea_options* opt, fea_plan_info* info, bool use_tuned) {
   if (!info) return fail(FEA_EINVAL, "info is NULL");

@@ -84,6 +84,7 @@ struct Req {
   int out_f32;
   int kind;          // kernel kind (batch dispatch)
   int64_t tile0;     // first global tile of this request (batch)
+  int64_t skip_copy; // test hook: 1 + the global tile whose input copy is skipped (0: none)
 };
 
 // Global assembly target of the one-pass kernel: the CSR values of the global

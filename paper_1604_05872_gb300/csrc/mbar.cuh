@@ -8,7 +8,7 @@
 namespace fea {
 
 constexpr unsigned ERR_TIMEOUT = 2u;
-constexpr long kMaxWaitIters = 1L << 20;  // try_wait polls: well under a second
+constexpr long kMaxWaitIters = 1L << 20;  // try_wait polls: about five seconds on GB300 before giving up
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));

@@ -377,24 +377,20 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
     // -------------------------------------------------------------- geometry
     const int gt = tid - 32 * C::W_GEO;  // 0 .. 95
     constexpr int NG_T = 32 * (C::W_EPI - C::W_GEO);
-    auto issue_inputs = [&](int64_t t, int ib) {
+    auto issue_inputs = [&](int64_t t, int ib) -> bool {
+      if (q.skip_copy == t + 1) return false;  // test hook: this tile's inputs never come
       const int64_t e0 = t * C::TE;
       const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       char* inb = sm + C::O_IN + (size_t)ib * C::IN_BUF;
       mbar_expect_tx(&bars->in_full[ib], (unsigned)(ne * (12 + C::CLEN) * 8));
       bulk_g2s(inb, q.coords + e0 * 12, (unsigned)(ne * 96), &bars->in_full[ib]);
       bulk_g2s(inb + C::TE * 96, q.coeffs + e0 * C::CLEN, (unsigned)(ne * C::CLEN * 8), &bars->in_full[ib]);
+      return true;
     };
     int pend0 = -1, pend1 = -1;  // iteration whose input copy is in flight, per buffer (leader thread)
     if (gt == 0) {
-      if (blockIdx.x < ntiles) {
-        issue_inputs(blockIdx.x, 0);
-        pend0 = 0;
-      }
-      if (blockIdx.x + (int64_t)gridDim.x < ntiles) {
-        issue_inputs(blockIdx.x + (int64_t)gridDim.x, 1);
-        pend1 = 1;
-      }
+      if (blockIdx.x < ntiles && issue_inputs(blockIdx.x, 0)) pend0 = 0;
+      if (blockIdx.x + (int64_t)gridDim.x < ntiles && issue_inputs(blockIdx.x + (int64_t)gridDim.x, 1)) pend1 = 1;
     }
     bool ok = true;
     int it = 0;
@@ -443,8 +439,7 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
         // the input buffer has been read: prefetch the tile two iterations ahead into it
         if (t + 2 * (int64_t)gridDim.x < ntiles) {
           fence_proxy_async();
-          issue_inputs(t + 2 * (int64_t)gridDim.x, b);
-          (b ? pend1 : pend0) = it + 2;
+          if (issue_inputs(t + 2 * (int64_t)gridDim.x, b)) (b ? pend1 : pend0) = it + 2;
         }
         mbar_arrive(&bars->geo_full[gb]);
       }

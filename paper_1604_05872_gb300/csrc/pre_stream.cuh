@@ -198,6 +198,7 @@ __device__ __forceinline__ void pre_stream_body(const Req& q, unsigned* err, con
   // one thread: bulk copies of the inputs of this CTA's j-th tile into buffer j & 1
   auto issue = [&](int j) {
     const int64_t e0 = (first + (int64_t)j * stride) * TE;
+    if (q.skip_copy == first + (int64_t)j * stride + 1) return;  // test hook: this tile's inputs never come
     const int ne = tile_ne(j), b = j & 1;
     double* dst = in + (size_t)b * TE * K::IN;
     const unsigned cb = (unsigned)ne * 96u, fb = (unsigned)ne * K::CLEN * 8u;
