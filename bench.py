@@ -242,6 +242,7 @@ WORKLOADS = {
     "mass_p1_10k": (0, 1, 10_000, False),
     "elasticity_p3_200k": (2, 3, 200_000, True),
     "neohookean_p2_500k": (3, 2, 500_000, False),
+    "neohookean_p3_100k": (3, 3, 100_000, False),
 }
 L2_BYTES = 129_000_000                                # GB300 L2 (129 MB)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flops x max clock
@@ -273,13 +274,17 @@ def precision_of(args, fea, form, p):
 
 
 def tc_flops_per_element(form, p):
-    """Useful tensor-core flops per element of the split-BF16 Neo-Hookean kernel:
-    rows = 2 x the symmetric basis pairs (hi and lo parts of the reference
-    tables), 9 columns (c, d) per element, K = 9 (Q + 1) (the points and the
-    point-summed term), two passes (hi and lo parts of H), 2 flops per MAC."""
+    """Useful tensor-core flops per element of the split-BF16 Neo-Hookean kernels,
+    2 flops per MAC.  P2 (reference tables as the shared operand): rows = 2 x the
+    symmetric basis pairs (hi and lo parts), 9 columns (c, d) per element,
+    K = 9 (Q + 1) (the points and the point-summed term), two passes (hi and lo
+    parts of H).  P3 (one product per element): the 3 n_s x 3 n_s blocks S and T
+    over the Q points, three split chains (hi hi, hi lo, lo hi)."""
     ns = (p + 1) * (p + 2) * (p + 3) // 6
     Q = (p + 1) ** 3
-    return 2 * 2 * (ns * (ns + 1)) * 9 * 9 * (Q + 1)
+    if p == 2:
+        return 2 * 2 * (ns * (ns + 1)) * 9 * 9 * (Q + 1)
+    return 2 * 3 * 2 * (3 * ns) ** 2 * Q
 
 
 def bf16_peak():

@@ -218,8 +218,9 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
   if (TE < 0) return fail(FEA_EINVAL, "negative tile");
   // tuned tiles were measured on the standalone kernels; the batch keeps its own rule
   if (k == tc) {
-    // the tensor-core kernel's layout fixes its tile (9 columns of the 128-column MMA per element)
-    if (TE != 0 && TE != tc->pref_tile) return fail(FEA_EINVAL, "the tensor-core kernel runs tiles of exactly 14 elements");
+    // the tensor-core kernel's layout fixes its tile (its accumulator columns per element)
+    if (TE != 0 && TE != tc->pref_tile)
+      return fail(FEA_EINVAL, "the tensor-core kernel runs tiles of exactly " + std::to_string(tc->pref_tile) + " elements");
     TE = tc->pref_tile;
   }
   if (TE == 0) TE = default_tile(variant, form, p, prec, k->max_tile, budget, Q, k->smem, use_tuned && !batch, k->pref_tile);

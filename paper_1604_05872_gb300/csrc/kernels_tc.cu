@@ -1,20 +1,26 @@
 // Tensor-core kernels of the split-operand precision (FEA_PREC_BF16X2) and the
-// device tables they read: the Neo-Hookean tangent at P2 (nh_tc.cuh).
+// device tables they read: the Neo-Hookean tangent at P2 (shared reference
+// operand, nh_tc.cuh) and at P3 (one product per element, nh_tce.cuh).
 #include <cstring>
 #include <vector>
 
 #include "host_model.h"
 #include "launch.cuh"
 #include "nh_tc.cuh"
+#include "nh_tce.cuh"
 
 namespace fea {
 
 template <int P>
 size_t nh_tc_smem(int, int) { return NhTc<P>::SMEM; }
+template <int P>
+size_t nh_tce_smem(int, int) { return NhTcE<P>::SMEM; }
 
 const KernelInfo kTcKernels[] = {
     KernelInfo{reinterpret_cast<const void*>(&nh_tc_kernel<2>), V_SE, NEOHOOKEAN, 2, 2, NhTc<2>::TE, &nh_tc_smem<2>,
                NhTc<2>::TE, NhTc<2>::NTH},
+    KernelInfo{reinterpret_cast<const void*>(&nh_tce_kernel<3>), V_SE, NEOHOOKEAN, 3, 2, NhTcE<3>::TE, &nh_tce_smem<3>,
+               NhTcE<3>::TE, NhTcE<3>::NTH},
 };
 const int kNumTcKernels = sizeof(kTcKernels) / sizeof(kTcKernels[0]);
 
@@ -82,10 +88,42 @@ static void nh_tc_table(std::vector<uint32_t>* words) {
   }
 }
 
+// W, dPhi and the symmetric point-summed tables Rbar_s[(a, b)][i] of the
+// per-element kernel: for (k, l) = (0,0), (0,1), (0,2), (1,1), (1,2), (2,2),
+// Rbar^kk and Rbar^kl + Rbar^lk with Rbar_ab^kl = sum_q w_q dPhi_a^k dPhi_b^l.
+template <int P>
+static void nh_tce_table(std::vector<uint32_t>* words) {
+  using C = NhTcE<P>;
+  const Tables t = make_tables(NEOHOOKEAN, P);
+  const TcETabLayout L = tce_tab_layout(C::Q, C::NS);
+  words->assign((size_t)L.total, 0u);
+  uint32_t* w = words->data();
+  for (int q = 0; q < C::Q; ++q) w[L.offW + q] = fbits(t.W[q]);
+  for (int i = 0; i < C::Q * C::NS * 3; ++i) w[L.offDphi + i] = fbits(t.dphi[i]);
+  auto g = [&](int q, int a, int k) { return t.dphi[((size_t)q * C::NS + a) * 3 + k]; };
+  for (int a = 0; a < C::NS; ++a)
+    for (int b = 0; b < C::NS; ++b) {
+      int i6 = 0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = k; l < 3; ++l, ++i6) {
+          double r = 0.0;
+          for (int q = 0; q < C::Q; ++q) {
+            r += t.W[q] * g(q, a, k) * g(q, b, l);
+            if (l != k) r += t.W[q] * g(q, a, l) * g(q, b, k);
+          }
+          w[L.offRbar + 6 * (a * C::NS + b) + i6] = fbits(r);
+        }
+    }
+}
+
 // Device-table words of the tensor-core kernel of (form, p); false if there is none.
 bool tc_table_words(int form, int p, std::vector<uint32_t>* words) {
   if (form == NEOHOOKEAN && p == 2) {
     nh_tc_table<2>(words);
+    return true;
+  }
+  if (form == NEOHOOKEAN && p == 3) {
+    nh_tce_table<3>(words);
     return true;
   }
   return false;

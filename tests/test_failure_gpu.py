@@ -24,7 +24,7 @@ def to_dev(coords, coeffs, form, p):
     return c, f
 
 
-@pytest.mark.parametrize("form,p,prec,E", [(1, 2, 1, 20000), (0, 3, 1, 9000), (3, 2, 2, 6000)])
+@pytest.mark.parametrize("form,p,prec,E", [(1, 2, 1, 20000), (0, 3, 1, 9000), (3, 2, 2, 6000), (3, 3, 2, 3000)])
 def test_skipped_input_copy_times_out_and_context_survives(fea, form, p, prec, E):
     coords, coeffs = inputs.workload(form, p, E, seed=4100 + 10 * form + p)
     c, f = to_dev(coords, coeffs, form, p)
@@ -46,7 +46,8 @@ def test_skipped_input_copy_times_out_and_context_survives(fea, form, p, prec, E
     (0, 4, 1, -1, False),                        # pre-evaluated tile kernel
     (2, 3, 1, 2, False), (2, 3, 1, 2, True),     # vector streaming kernel
     (3, 3, 1, -1, False),                        # vector sharing-elimination tile kernel
-    (3, 2, 2, -1, False), (3, 2, 2, -1, True),   # tensor-core kernel
+    (3, 2, 2, -1, False), (3, 2, 2, -1, True),   # tensor-core kernel, shared reference operand
+    (3, 3, 2, -1, False), (3, 3, 2, -1, True),   # tensor-core kernel, one product per element
     (1, 3, 0, -1, False),                        # FP64 path
     (2, 2, 0, 0, False),                         # plain FP64 comparator
 ])
