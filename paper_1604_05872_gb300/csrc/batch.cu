@@ -131,6 +131,7 @@ const void* table_ptr(DevState* st, int form, int p, int prec, int* rc);
 int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch);
 int set_error(int code, const char* msg);
 int check_device_ptr(const void* p, const char* what, bool allow_null);
+cudaError_t issue_launch_raw(PreparedLaunch& L, cudaStream_t stream);
 int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, const double* coords,
                    const double* coeffs, void* out, int out_f32, PreparedLaunch* L);
 
@@ -332,8 +333,7 @@ int batch_impl(const fea_request* reqs, int nreq, const fea_options* opt, void* 
       for (int b = 1; b < kBranches; ++b)
         if (load[b] < load[k]) k = b;
       load[k] += work[i].first;
-      void* args[] = {&L[i].q, &L[i].err};
-      e = cudaLaunchKernel(L[i].fn, dim3(L[i].grid), dim3(L[i].threads), args, L[i].smem, bs->br[k]);
+      e = issue_launch_raw(L[i], bs->br[k]);
     }
     for (int k = 1; k < kBranches && e == cudaSuccess; ++k) {
       e = cudaEventRecord(bs->ev[k], bs->br[k]);

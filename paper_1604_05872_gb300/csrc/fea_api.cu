@@ -54,6 +54,12 @@ struct DevState {
   size_t ws_bytes[2][3] = {{0, 0, 0}, {0, 0, 0}};
   // batch
   BatchState* batch = nullptr;
+  // tile counters of the kernels that hand out tiles dynamically: one per stream that
+  // launches them (launches on one stream run in order, so its counter is reset before
+  // each and never shared with a launch in flight on another stream)
+  static constexpr int kCounters = 64;
+  unsigned long long* ctr = nullptr;
+  std::map<cudaStream_t, int> ctr_slot;
 };
 
 static std::mutex g_mu;
@@ -73,6 +79,8 @@ static int get_dev(DevState** out) {
     st->smem_optin = prop.sharedMemPerBlockOptin;
     CUDA_TRY(cudaMalloc(&st->err, sizeof(unsigned)));
     CUDA_TRY(cudaMemset(st->err, 0, sizeof(unsigned)));
+    CUDA_TRY(cudaMalloc(&st->ctr, DevState::kCounters * sizeof(unsigned long long)));
+    CUDA_TRY(cudaMemset(st->ctr, 0, DevState::kCounters * sizeof(unsigned long long)));
     it = g_dev.emplace(dev, std::move(st)).first;
   }
   *out = it->second.get();
@@ -288,6 +296,7 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
   q.kind = 0;
   q.tile0 = 0;
   q.skip_copy = g_skip_copy.exchange(0);  // test hook, one launch only
+  q.tile_ctr = nullptr;                   // set per launch (issue_launch_raw)
   const int64_t ntiles = (E + tile - 1) / tile;
   int per_sm = 0;
   {
@@ -318,12 +327,41 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
   L->smem = smem_bytes;
   L->q = q;
   L->err = st->err;
+  L->dyn = pl.k->dyn_tiles;
+  L->st = st;
   return FEA_OK;
 }
 
+// The tile counter of `stream` (assigned on first use, no allocation), or null
+// once every counter has a stream: the kernel then runs its static schedule.
+static unsigned long long* tile_counter(DevState* st, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = st->ctr_slot.find(stream);
+  if (it == st->ctr_slot.end()) {
+    if ((int)st->ctr_slot.size() >= DevState::kCounters) return nullptr;
+    it = st->ctr_slot.emplace(stream, (int)st->ctr_slot.size()).first;
+  }
+  return st->ctr + it->second;
+}
+
+// Launch a prepared kernel on `stream`; a kernel that hands out its tiles
+// dynamically gets its stream's counter, zeroed on the stream just before.
+cudaError_t issue_launch_raw(PreparedLaunch& L, cudaStream_t stream) {
+  Req q = L.q;
+  q.tile_ctr = nullptr;
+  if (L.dyn && L.st) {
+    q.tile_ctr = tile_counter(L.st, stream);
+    if (q.tile_ctr) {
+      const cudaError_t e = cudaMemsetAsync(q.tile_ctr, 0, sizeof(unsigned long long), stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  void* args[] = {&q, &L.err};
+  return cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.threads), args, L.smem, stream);
+}
+
 int issue_launch(PreparedLaunch& L, cudaStream_t stream) {
-  void* args[] = {&L.q, &L.err};
-  CUDA_TRY(cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.threads), args, L.smem, stream));
+  CUDA_TRY(issue_launch_raw(L, stream));
   return FEA_OK;
 }
 
@@ -552,6 +590,7 @@ void finalize_impl() {
     }
     free_batch_state(st->batch);
     cudaFree(st->err);
+    cudaFree(st->ctr);
   }
   g_dev.clear();
   cudaSetDevice(cur);

@@ -13,6 +13,7 @@ struct KernelInfo {
   size_t (*smem)(int TE, int Q);      // dynamic shared memory for a tile of TE
   int pref_tile;                      // tile the thread layout is built for (0: none)
   int threads = 0;                    // threads per CTA (0: NT)
+  bool dyn_tiles = false;             // takes its tiles from Req::tile_ctr when one is given
 };
 
 // Registered by the kernel translation units.

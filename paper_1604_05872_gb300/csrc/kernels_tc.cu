@@ -20,7 +20,7 @@ const KernelInfo kTcKernels[] = {
     KernelInfo{reinterpret_cast<const void*>(&nh_tc_kernel<2>), V_SE, NEOHOOKEAN, 2, 2, NhTc<2>::TE, &nh_tc_smem<2>,
                NhTc<2>::TE, NhTc<2>::NTH},
     KernelInfo{reinterpret_cast<const void*>(&nh_tce_kernel<3>), V_SE, NEOHOOKEAN, 3, 2, NhTcE<3>::TE, &nh_tce_smem<3>,
-               NhTcE<3>::TE, NhTcE<3>::NTH},
+               NhTcE<3>::TE, NhTcE<3>::NTH, true},
 };
 const int kNumTcKernels = sizeof(kTcKernels) / sizeof(kTcKernels[0]);
 

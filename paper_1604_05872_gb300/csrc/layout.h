@@ -85,6 +85,8 @@ struct Req {
   int kind;          // kernel kind (batch dispatch)
   int64_t tile0;     // first global tile of this request (batch)
   int64_t skip_copy; // test hook: 1 + the global tile whose input copy is skipped (0: none)
+  unsigned long long* tile_ctr;  // tiles handed out by an atomic counter zeroed before the launch
+                                 // (kernels that support it), or null: tiles blockIdx.x + k gridDim.x
 };
 
 // Global assembly target of the one-pass kernel: the CSR values of the global

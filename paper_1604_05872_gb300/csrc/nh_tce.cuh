@@ -42,6 +42,12 @@
 //                 T rows scattered block-transposed into an FP32 staging
 //                 matrix, then S rows (and Mu) added in place, then coalesced
 //                 16-byte stores.
+// Tiles are handed out by an atomic counter when the launch provides one (so a
+// CTA on a faster SM takes more of them), else CTA c takes tiles c, c + grid, ...
+// The geometry warp draws them, two iterations ahead, into a ring in shared
+// memory; every role reads iteration i's tile there after the wait that hands it
+// iteration i.  Past the last tile the ring holds -1: each role passes that mark
+// on through the signal its consumer waits for, then leaves.
 // Every mbarrier wait is bounded; a role that gives up sets the error word, the
 // others then give up too, and the CTA waits for its copies and MMAs in flight
 // before it frees the tensor memory and leaves.
@@ -105,7 +111,9 @@ struct NhTcE {
   static constexpr size_t O_W = O_GEO + NGB * (size_t)TE * 24 * 4;
   static constexpr size_t O_DPHI = O_W + round_up_sz((size_t)Q * 4, 16);
   static constexpr size_t O_BAR = O_DPHI + (size_t)Q * RS * 4;
-  static constexpr size_t SMEM = O_BAR + 256 + 128;  // + alignment of the base to 128 bytes
+  static constexpr int NRING = 16;                    // tiles of the coming iterations (see the geometry role)
+  static constexpr size_t O_RING = O_BAR + 256;
+  static constexpr size_t SMEM = O_RING + NRING * 8 + 128;  // + alignment of the base to 128 bytes
   static_assert(SMEM <= 232448, "shared memory per CTA");
   static_assert(O_STAGE % 16 == 0 && O_MU % 16 == 0 && O_PW % 16 == 0 && O_IN % 16 == 0 && O_UT % 16 == 0 &&
                     O_GEO % 16 == 0 && O_DPHI % 16 == 0 && O_BAR % 16 == 0,
@@ -240,6 +248,7 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
   NhTcEBars* bars = reinterpret_cast<NhTcEBars*>(sm + C::O_BAR);
   float* sW = reinterpret_cast<float*>(sm + C::O_W);
   float* sD = reinterpret_cast<float*>(sm + C::O_DPHI);
+  volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(sm + C::O_RING);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (q.E + C::TE - 1) / C::TE;
   const float* tab = static_cast<const float*>(q.tab);
@@ -300,12 +309,17 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
       constexpr uint32_t idesc = idesc_f16kind(1u, 128u, (uint32_t)C::NCOL);
       const uint32_t op0 = smem_addr(sm + C::O_OP);
       bool ok = true;
-      int it = 0;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+      for (int it = 0;; ++it) {
         const int buf = it & 1;
         ok = it < 2 || mbar_wait_sleep(&bars->d_empty[buf], (unsigned)(((it >> 1) - 1) & 1));
+        if (ok) ok = mbar_wait_sleep(&bars->op_full[0], (unsigned)(it & 1));
+        if (!ok) break;
+        if (ring[it % C::NRING] < 0) {  // past the last tile: let the epilogue see it too
+          tc_commit(&bars->d_full[buf]);
+          break;
+        }
         for (int e = 0; e < C::TE && ok; ++e) {
-          ok = mbar_wait_sleep(&bars->op_full[e], (unsigned)(it & 1));
+          if (e > 0) ok = mbar_wait_sleep(&bars->op_full[e], (unsigned)(it & 1));
           if (!ok) break;
           tc_fence_after();
           const uint32_t dt = tb + (uint32_t)(buf * C::TE + e) * C::NCOL;
@@ -344,24 +358,54 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
       bulk_g2s(inb + C::TE * 96, q.coeffs + e0 * C::CLEN, (unsigned)(ne * C::CLEN * 8), &bars->in_full[ib]);
       return true;
     };
+    // lane 0: the tile of this CTA's next iteration, -1 past the last one (draws are monotonic)
+    bool drawn_out = false;
+    int64_t next_static = blockIdx.x;
+    auto draw = [&]() -> int64_t {
+      if (drawn_out) return -1;
+      const int64_t t = q.tile_ctr ? (int64_t)atomicAdd(q.tile_ctr, 1ull) : next_static;
+      next_static += gridDim.x;
+      if (t >= ntiles) {
+        drawn_out = true;
+        return -1;
+      }
+      return t;
+    };
     int pend0 = -1, pend1 = -1;  // iteration whose input copy is in flight, per buffer (lane 0)
     if (lane == 0) {
-      if (blockIdx.x < ntiles && issue_inputs(blockIdx.x, 0)) pend0 = 0;
-      if (blockIdx.x + (int64_t)gridDim.x < ntiles && issue_inputs(blockIdx.x + (int64_t)gridDim.x, 1)) pend1 = 1;
+      const int64_t t0 = draw();
+      ring[0] = t0;
+      if (t0 >= 0 && issue_inputs(t0, 0)) pend0 = 0;
+      const int64_t t1 = draw();
+      ring[1] = t1;
+      if (t1 >= 0 && issue_inputs(t1, 1)) pend1 = 1;
     }
+    __syncwarp();
     bool ok = true;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
+      const int64_t t = ring[it % C::NRING];
       const int b = it & 1, gb = it % 3;
-      const int64_t e0 = t * C::TE;
-      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       unsigned w = 1;
       if (lane == 0) {
-        w = mbar_wait_sleep(&bars->in_full[b], (unsigned)((it >> 1) & 1));
+        if (t >= 0) w = mbar_wait_sleep(&bars->in_full[b], (unsigned)((it >> 1) & 1));
         if (w && it >= 3) w = mbar_wait_sleep(&bars->geo_empty[gb], (unsigned)((it / 3 - 1) & 1));
       }
       ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       if (!ok) break;
+      if (t < 0) {
+        // past the last tile: both kinematics groups learn it (this iteration and the next)
+        if (lane == 0) {
+          mbar_arrive(&bars->geo_full[gb]);
+          const int i1 = it + 1;
+          w = i1 < 3 || mbar_wait_sleep(&bars->geo_empty[i1 % 3], (unsigned)((i1 / 3 - 1) & 1));
+          ring[i1 % C::NRING] = -1;
+          if (w) mbar_arrive(&bars->geo_full[i1 % 3]);
+        }
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+        break;
+      }
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       if (lane == 0) (b ? pend1 : pend0) = -1;
       const double* xs = reinterpret_cast<const double*>(sm + C::O_IN + (size_t)b * C::IN_BUF);
       const double* us = xs + C::TE * 12;
@@ -396,10 +440,12 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
       }
       __syncwarp();
       if (lane == 0) {
-        // the input buffer has been read: prefetch the tile two iterations ahead into it
-        if (t + 2 * (int64_t)gridDim.x < ntiles) {
+        // the input buffer has been read: draw the tile two iterations ahead and prefetch it into it
+        const int64_t t2 = draw();
+        ring[(it + 2) % C::NRING] = t2;
+        if (t2 >= 0) {
           fence_proxy_async();
-          if (issue_inputs(t + 2 * (int64_t)gridDim.x, b)) (b ? pend1 : pend0) = it + 2;
+          if (issue_inputs(t2, b)) (b ? pend1 : pend0) = it + 2;
         }
         mbar_arrive(&bars->geo_full[gb]);
       }
@@ -419,10 +465,7 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
     float* pw = reinterpret_cast<float*>(sm + C::O_PW + (size_t)gk * C::PW_SLOT);
     float* pwk = pw + C::TE * C::PW_E;
     bool ok = true;
-    int it = gk;
-    for (int64_t t = blockIdx.x + (int64_t)gk * gridDim.x; t < ntiles; t += 2 * (int64_t)gridDim.x, it += 2) {
-      const int64_t e0 = t * C::TE;
-      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
+    for (int it = gk;; it += 2) {
       const int gb = it % 3;
       const float* ut = reinterpret_cast<const float*>(sm + C::O_UT) + gb * C::TE * C::RU;
       const float* geo = reinterpret_cast<const float*>(sm + C::O_GEO) + gb * C::TE * 24;
@@ -430,6 +473,13 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
       if (w && it >= 2) w = mbar_wait_sleep(&bars->pw_empty[gk], (unsigned)(((it >> 1) - 1) & 1));
       ok = named_and(bar_id, 128, w);
       if (!ok) break;
+      const int64_t t = ring[it % C::NRING];
+      if (t < 0) {  // past the last tile: pass it on to the operand warps
+        if (lane == 0) mbar_arrive(&bars->pw_full[gk]);
+        break;
+      }
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       if (kt < ne * 6) pwk[8 * (kt / 6) + kt % 6] = geo[24 * (kt / 6) + 12 + kt % 6];
       for (int w2 = kt; w2 < ne * C::Q; w2 += 128) {
         const int e = w2 / C::Q, qq = w2 - e * C::Q;
@@ -528,15 +578,27 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
                                sD[(8 * o + 2 * j + 1) * C::RS + C::node_slot(a, k)]);
     float* mu_tab = reinterpret_cast<float*>(sm + C::O_MU);
     bool ok = true;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
       const int slot = it & 1, buf = it & 1;
-      const int64_t e0 = t * C::TE;
-      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       unsigned w = 1;
       if (lane == 0) w = mbar_wait_sleep(&bars->pw_full[slot], (unsigned)((it >> 1) & 1));
       ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       if (!ok) break;
+      const int64_t t = ring[it % C::NRING];
+      if (t < 0) {
+        // past the last tile: pass it on to the MMA warp (operand slot 0) and to the epilogue
+        // (Mu table), each after the wait that keeps the barrier phases in step
+        if (lane == 0) {
+          w = it < 1 || mbar_wait_sleep(&bars->op_empty[0], (unsigned)((it - 1) & 1));
+          if (w) mbar_arrive(&bars->op_full[0]);
+          if (w) w = it < 2 || mbar_wait_sleep(&bars->d_empty[buf], (unsigned)(((it >> 1) - 1) & 1));
+          if (w) mbar_arrive(&bars->mu_full[buf]);
+        }
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+        break;
+      }
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       const float* pw = reinterpret_cast<const float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT);
       for (int e = 0; e < C::TE; ++e) {
         if (lane == 0 && it >= 1) w = mbar_wait_sleep(&bars->op_empty[e], (unsigned)((it - 1) & 1));
@@ -579,15 +641,16 @@ __global__ void __launch_bounds__(NhTcE<P>::NTH, 1) nh_tce_kernel(Req q, unsigne
     static_assert(C::N3 == 60, "pair stepping of the output loop");
     const int soff0 = (et / 30) * C::LD + 2 * (et % 30);
     bool ok = true;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
       const int buf = it & 1;
-      const int64_t e0 = t * C::TE;
-      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       bool w = mbar_wait_sleep(&bars->d_full[buf], (unsigned)((it >> 1) & 1));
       if (w) w = mbar_wait_sleep(&bars->mu_full[buf], (unsigned)((it >> 1) & 1));
       ok = named_and(bar, 128, w);
       if (!ok) break;
+      const int64_t t = ring[it % C::NRING];
+      if (t < 0) break;  // past the last tile
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       tc_fence_after();
 #pragma unroll 1
       for (int j = 0; j < 2; ++j) {

@@ -20,6 +20,7 @@ struct Plan {
 };
 
 // A launch resolved on the host (kernel, persistent grid, shared memory, request).
+struct DevState;
 struct PreparedLaunch {
   const void* fn = nullptr;
   unsigned grid = 0;
@@ -27,6 +28,8 @@ struct PreparedLaunch {
   size_t smem = 0;
   Req q{};
   unsigned* err = nullptr;
+  bool dyn = false;         // the kernel takes a tile counter (zeroed on the launch stream first)
+  DevState* st = nullptr;   // owner of the per-stream tile counters
 };
 
 // Per-element operation counts (adds and products; an FMA counts 2) of the
