@@ -18,7 +18,7 @@ size_t nh_tce_smem(int, int) { return NhTcE<P>::SMEM; }
 
 const KernelInfo kTcKernels[] = {
     KernelInfo{reinterpret_cast<const void*>(&nh_tc_kernel<2>), V_SE, NEOHOOKEAN, 2, 2, NhTc<2>::TE, &nh_tc_smem<2>,
-               NhTc<2>::TE, NhTc<2>::NTH},
+               NhTc<2>::TE, NhTc<2>::NTH, true},
     KernelInfo{reinterpret_cast<const void*>(&nh_tce_kernel<3>), V_SE, NEOHOOKEAN, 3, 2, NhTcE<3>::TE, &nh_tce_smem<3>,
                NhTcE<3>::TE, NhTcE<3>::NTH, true},
 };

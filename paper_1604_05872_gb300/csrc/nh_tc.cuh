@@ -46,7 +46,11 @@
 //   warps 20-27  build H, one row (e, c, d) per thread, two groups of four
 //                taking half of the points each; split into BF16 hi/lo.
 // R (128 rows x K/2 packed BF16 pairs) sits in tensor memory for the whole
-// launch; D is double-buffered in tensor memory.  Every mbarrier wait is
+// launch; D is double-buffered in tensor memory.  Tiles come from an atomic
+// counter when the launch provides one (else CTA c takes c, c + grid, ...): the
+// geometry leader draws them two iterations ahead into a ring in shared memory
+// that every role reads after the wait that hands it the iteration; -1 past the
+// last tile is passed from role to role.  Every mbarrier wait is
 // bounded; a role that gives up sets the error word, the others then give up
 // too, and the CTA waits for its copies and MMAs in flight before it frees the
 // tensor memory and leaves.
@@ -135,6 +139,10 @@ struct NhTcBars {
       d_empty[2], done;
   uint32_t tbase;
 };
+// Tiles of the coming iterations (see the geometry role), in the barrier block's spare bytes.
+constexpr int kNhTcRing = 16;
+constexpr size_t kNhTcRingOff = 192;
+static_assert(sizeof(NhTcBars) <= kNhTcRingOff && kNhTcRingOff + kNhTcRing * 4 <= 256, "tile ring");
 
 // Elements EL0 .. EL0 + NEL - 1 of a half tile whose first element is e0 and
 // whose accumulator columns start at dcol (of which the first nel exist: fewer
@@ -265,6 +273,7 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
   }
   char* sm = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   NhTcBars* bars = reinterpret_cast<NhTcBars*>(sm + C::O_BAR);
+  volatile int* ring = reinterpret_cast<volatile int*>(sm + C::O_BAR + kNhTcRingOff);
   float* sW = reinterpret_cast<float*>(sm + C::O_W);
   float* sD = reinterpret_cast<float*>(sm + C::O_DPHI);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -346,14 +355,19 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       constexpr uint32_t idesc = idesc_f16kind(1u, 128u, (uint32_t)C::NCOL);
       const uint32_t hhi = smem_addr(sm + C::O_HHI), hlo = smem_addr(sm + C::O_HLO);
       bool ok = true;
-      int it = 0;
-      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      for (int it = 0;; ++it) {
         const int buf = it & 1;
         ok = it < 2 || mbar_wait_sleep(&bars->d_empty[buf], (unsigned)(((it >> 1) - 1) & 1));
+        if (ok) ok = mbar_wait_sleep(&bars->h_full[0], (unsigned)(it & 1));
+        if (!ok) break;
+        if (ring[it % kNhTcRing] < 0) {  // past the last tile: let the epilogue see it too
+          tc_commit(&bars->d_full[buf]);
+          break;
+        }
         const uint32_t dt = tb + (uint32_t)buf * 128u;
         // the two halves of K, written by the two builder groups (K steps 0 .. KSA - 1, KSA .. KS - 1)
         for (int h = 0; h < 2 && ok; ++h) {
-          ok = mbar_wait_sleep(&bars->h_full[h], (unsigned)(it & 1));
+          if (h > 0) ok = mbar_wait_sleep(&bars->h_full[h], (unsigned)(it & 1));
           if (!ok) break;
           tc_fence_after();
           const int j0 = h == 0 ? 0 : C::KSA, j1 = h == 0 ? C::KSA : C::KS;
@@ -387,21 +401,47 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       bulk_g2s(inb + C::TE * 96, q.coeffs + e0 * C::CLEN, (unsigned)(ne * C::CLEN * 8), &bars->in_full[ib]);
       return true;
     };
+    // leader: the tile of this CTA's next iteration, -1 past the last one (draws are monotonic)
+    bool drawn_out = false;
+    int64_t next_static = blockIdx.x;
+    auto draw = [&]() -> int {
+      if (drawn_out) return -1;
+      const int64_t t = q.tile_ctr ? (int64_t)atomicAdd(q.tile_ctr, 1ull) : next_static;
+      next_static += gridDim.x;
+      if (t >= ntiles) {
+        drawn_out = true;
+        return -1;
+      }
+      return (int)t;
+    };
     int pend0 = -1, pend1 = -1;  // iteration whose input copy is in flight, per buffer (leader thread)
     if (gt == 0) {
-      if (blockIdx.x < ntiles && issue_inputs(blockIdx.x, 0)) pend0 = 0;
-      if (blockIdx.x + (int64_t)gridDim.x < ntiles && issue_inputs(blockIdx.x + (int64_t)gridDim.x, 1)) pend1 = 1;
+      const int t0 = draw();
+      ring[0] = t0;
+      if (t0 >= 0 && issue_inputs(t0, 0)) pend0 = 0;
+      const int t1 = draw();
+      ring[1] = t1;
+      if (t1 >= 0 && issue_inputs(t1, 1)) pend1 = 1;
     }
+    named_sync(C::BAR_GEO, NG_T);
     bool ok = true;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
+      const int64_t t = ring[it % kNhTcRing];
       const int b = it & 1, gb = it % 3;
+      bool w = t < 0 || mbar_wait_sleep(&bars->in_full[b], (unsigned)((it >> 1) & 1));
+      if (w && it >= 3) w = mbar_wait_sleep(&bars->geo_empty[gb], (unsigned)((it / 3 - 1) & 1));
+      if (t < 0 && w && gt == 0) {
+        // past the last tile: both kinematics groups learn it (this iteration and the next)
+        mbar_arrive(&bars->geo_full[gb]);
+        const int i1 = it + 1;
+        w = i1 < 3 || mbar_wait_sleep(&bars->geo_empty[i1 % 3], (unsigned)((i1 / 3 - 1) & 1));
+        ring[i1 % kNhTcRing] = -1;
+        if (w) mbar_arrive(&bars->geo_full[i1 % 3]);
+      }
+      ok = named_and(C::BAR_GEO, NG_T, w);
+      if (!ok || t < 0) break;
       const int64_t e0 = t * C::TE;
       const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
-      bool w = mbar_wait_sleep(&bars->in_full[b], (unsigned)((it >> 1) & 1));
-      if (w && it >= 3) w = mbar_wait_sleep(&bars->geo_empty[gb], (unsigned)((it / 3 - 1) & 1));
-      ok = named_and(C::BAR_GEO, NG_T, w);
-      if (!ok) break;
       if (gt == 0) (b ? pend1 : pend0) = -1;
       const double* xs = reinterpret_cast<const double*>(sm + C::O_IN + (size_t)b * C::IN_BUF);
       const double* us = xs + C::TE * 12;
@@ -436,10 +476,12 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       }
       named_sync(C::BAR_GEO, NG_T);
       if (gt == 0) {
-        // the input buffer has been read: prefetch the tile two iterations ahead into it
-        if (t + 2 * (int64_t)gridDim.x < ntiles) {
+        // the input buffer has been read: draw the tile two iterations ahead and prefetch it into it
+        const int t2 = draw();
+        ring[(it + 2) % kNhTcRing] = t2;
+        if (t2 >= 0) {
           fence_proxy_async();
-          if (issue_inputs(t + 2 * (int64_t)gridDim.x, b)) (b ? pend1 : pend0) = it + 2;
+          if (issue_inputs(t2, b)) (b ? pend1 : pend0) = it + 2;
         }
         mbar_arrive(&bars->geo_full[gb]);
       }
@@ -468,13 +510,14 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
     float* stage = reinterpret_cast<float*>(sm + C::O_STAGE + (size_t)set * round_up_sz((size_t)C::ES * C::NN * 4, 16));
     const uint32_t trow = tb + ((uint32_t)(32 * qd) << 16);
     bool ok = true;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
       const int buf = it & 1;
-      const int64_t e0 = t * C::TE;
-      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       ok = named_and(bar, 128, mbar_wait_sleep(&bars->d_full[buf], (unsigned)((it >> 1) & 1)));
       if (!ok) break;
+      const int64_t t = ring[it % kNhTcRing];
+      if (t < 0) break;  // past the last tile
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       tc_fence_after();
       const uint32_t dcol = trow + (uint32_t)buf * 128u;
       static_assert(C::EH == 7 && C::ES == 4 && 9 * C::EH < 64, "epilogue parts");
@@ -491,10 +534,7 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
     const int kt = tid - 32 * C::W_KIN - 128 * gk;
     const int bar_id = C::BAR_KIN + gk;
     bool ok = true;
-    int it = gk;
-    for (int64_t t = blockIdx.x + (int64_t)gk * gridDim.x; t < ntiles; t += 2 * (int64_t)gridDim.x, it += 2) {
-      const int64_t e0 = t * C::TE;
-      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
+    for (int it = gk;; it += 2) {
       const int gb = it % 3, slot = gb;  // geometry buffer and pointwise slot of this iteration
       const float* ut = reinterpret_cast<const float*>(sm + C::O_UT) + gb * C::TE * C::RU;
       float* pw = reinterpret_cast<float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT);
@@ -504,6 +544,13 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       if (w && it >= 3) w = mbar_wait_sleep(&bars->pw_empty[slot], (unsigned)((it / 3 - 1) & 1));
       ok = named_and(bar_id, 128, w);
       if (!ok) break;
+      const int64_t t = ring[it % kNhTcRing];
+      if (t < 0) {  // past the last tile: pass it on to the H builders
+        if (lane == 0) mbar_arrive(&bars->pw_full[slot]);
+        break;
+      }
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       if (kt < ne) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) pwk[9 * kt + k] = geo[24 * kt + 12 + k];
@@ -602,11 +649,8 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
     char* hlo = sm + C::O_HLO + (size_t)(n >> 3) * C::SBO + (size_t)(n & 7) * 16;
     static_assert(C::NG == 4, "two point groups per builder half");
     bool ok = true;
-    int it = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
       const int slot = it % 3;
-      const int64_t e0 = t * C::TE;
-      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       unsigned w = 1;
       if (lane == 0) {
         w = mbar_wait_sleep(&bars->pw_full[slot], (unsigned)((it / 3) & 1));
@@ -615,6 +659,13 @@ __global__ void __launch_bounds__(NhTc<P>::NTH, 1) nh_tc_kernel(Req q, unsigned*
       }
       ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       if (!ok) break;
+      const int64_t t = ring[it % kNhTcRing];
+      if (t < 0) {  // past the last tile: pass it on to the MMA warp
+        if (lane == 0) mbar_arrive(&bars->h_full[gb]);
+        break;
+      }
+      const int64_t e0 = t * C::TE;
+      const int ne = (int)(q.E - e0 < C::TE ? q.E - e0 : C::TE);
       if (e < ne) {
         const float* rec = reinterpret_cast<const float*>(sm + C::O_PW + (size_t)slot * C::PW_SLOT) + e * C::PW_E;
         const float* pwk = reinterpret_cast<const float*>(sm + C::O_PWK) + slot * C::TE * 9 + 9 * e;
