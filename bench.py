@@ -56,6 +56,9 @@ PROFILES = {
     "neohookean_p2_500k@bf16x2": ("neohookean_p2_tc_500k.md",
                                   ["common.cuh", "layout.h", "launch.cuh", "mbar.cuh", "tc.cuh", "nh_tc.cuh",
                                    "log_f64.cuh", "log_table.h", "kernels_tc.cu"]),
+    "neohookean_p3_100k@bf16x2": ("neohookean_p3_tc_100k.md",
+                                  ["common.cuh", "layout.h", "launch.cuh", "mbar.cuh", "tc.cuh", "nh_tce.cuh",
+                                   "log_f64.cuh", "log_table.h", "kernels_tc.cu"]),
     "helmholtz_p2_global_1M": ("global_helmholtz_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh", "planner.cpp"]),
     "helmholtz_load_p2_1M": ("helmholtz_load_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh"]),
     "neohookean_residual_p2_500k": ("neohookean_residual_p2_500k.md",
