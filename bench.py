@@ -469,7 +469,8 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         roof["tensor_frac"] = roof["tensor_achieved_tflops"] / bf16
     cfg = {"workload": args.workload, "form": ["mass", "helmholtz", "elasticity", "neohookean"][form],
            "degree": p, "elements": E, "quad_points": pl["quad_points"], "local_matrix": "%dx%d %s" % (n, n, "f32" if f32 else "f64"),
-           "variant": fea.VARIANT_NAMES[pl["variant"]] + (" (per-point pre-evaluation on tcgen05)" if tc else ""),
+           "variant": fea.VARIANT_NAMES[pl["variant"]] + ((" (per-point pre-evaluation on tcgen05)" if p == 2 else
+                                                          " (one S, T product per element on tcgen05)") if tc else ""),
            "tile": pl["tile"], "geometry": "f64",
            "contraction": "bf16x2 split operands on tcgen05 tensor cores, f32 accumulation" if tc else prec_name,
            "parallelism": "dp%d (element shards)" % world,
