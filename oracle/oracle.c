@@ -23,6 +23,9 @@
  *   vector DOFs    row/column index 3*a + c (scalar node a, component c).
  *   output         A[e][i][j] row-major, i = test, j = trial.
  *
+ * The Bernstein-Bezier basis (the variant computed by sum factorisation on
+ * the device) is evaluated here from its definition, for the same two forms.
+ *
  * Parity of the Neo-Hookean tangent is pinned by finite differences of this
  * file's own residual and energy (both written from the strain energy), not by
  * a closed form; every other form has closed-form or invariant pins in tests/.
@@ -551,6 +554,131 @@ int oracle_neohookean_energy(int p, int m, int64_t E, const double *coords,
   }
   free(X); free(W); free(phi); free(dphi);
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bernstein-Bezier basis (the sum-factorised variant): the definition.      */
+/* ------------------------------------------------------------------------ */
+/* B_a = p! / (a0! a1! a2! a3!) l0^a0 l1^a1 l2^a2 l3^a3 over |a| = p, ordered
+ * a3 = 0..p (slowest), then a2 = 0..p-a3, then a1 = 0..p-a3-a2 (fastest),
+ * a0 = p - a1 - a2 - a3.  The order is an interface convention; the values
+ * here come from the definition only. */
+int oracle_bernstein_indices(int p, int *alpha) {
+  int k = 0;
+  for (int a3 = 0; a3 <= p; ++a3)
+    for (int a2 = 0; a2 <= p - a3; ++a2)
+      for (int a1 = 0; a1 <= p - a3 - a2; ++a1) {
+        alpha[4 * k + 0] = p - a1 - a2 - a3;
+        alpha[4 * k + 1] = a1;
+        alpha[4 * k + 2] = a2;
+        alpha[4 * k + 3] = a3;
+        ++k;
+      }
+  return k;
+}
+
+static double factorial(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= (double)i;
+  return f;
+}
+
+static double ipow(double x, int n) {
+  double r = 1.0;
+  for (int i = 0; i < n; ++i) r *= x;
+  return r;
+}
+
+/* B [Q][n] and dB/dX [Q][n][3] at reference points X [Q][3]. */
+int oracle_bernstein_basis(int p, int Q, const double *X, double *B, double *dB) {
+  const int n = oracle_nbasis(p);
+  int *al = (int *)malloc(sizeof(int) * 4 * n);
+  oracle_bernstein_indices(p, al);
+  for (int q = 0; q < Q; ++q) {
+    const double l[4] = {1.0 - X[3 * q] - X[3 * q + 1] - X[3 * q + 2], X[3 * q], X[3 * q + 1], X[3 * q + 2]};
+    for (int k = 0; k < n; ++k) {
+      const int *a = al + 4 * k;
+      const double c = factorial(p) / (factorial(a[0]) * factorial(a[1]) * factorial(a[2]) * factorial(a[3]));
+      double v = c;
+      for (int j = 0; j < 4; ++j) v *= ipow(l[j], a[j]);
+      B[(size_t)q * n + k] = v;
+      /* dB/dl_j = c a_j l^(a - e_j); dB/dX_i = dB/dl_{i+1} - dB/dl_0 */
+      double dl[4];
+      for (int j = 0; j < 4; ++j) {
+        if (a[j] == 0) {
+          dl[j] = 0.0;
+          continue;
+        }
+        double t = c * (double)a[j];
+        for (int i = 0; i < 4; ++i) t *= ipow(l[i], a[i] - (i == j ? 1 : 0));
+        dl[j] = t;
+      }
+      for (int i = 0; i < 3; ++i) dB[((size_t)q * n + k) * 3 + i] = dl[i + 1] - dl[0];
+    }
+  }
+  free(al);
+  return n;
+}
+
+/* Element matrices in the Bernstein basis by the plain quadrature nest:
+ * mass A_ij = sum_q w_q |det J| B_i B_j; Helmholtz
+ * A_ij = sum_q w_q |det J| (G_i . G_j + f_q B_i B_j) with f_q = sum_k c_k B_k(X_q)
+ * (c: the Bernstein coefficients of f, [E][n]) and G = J^-T grad_X B. */
+int oracle_assemble_bernstein(int form, int p, int m, int64_t E, const double *coords, const double *c,
+                              double *out, int nthreads) {
+  if ((form != OR_MASS && form != OR_HELMHOLTZ) || p < 1 || p > 4) return -1;
+  const int n = oracle_nbasis(p);
+  const int Q = oracle_rule_size(m);
+  double *X = (double *)malloc(sizeof(double) * 3 * Q);
+  double *W = (double *)malloc(sizeof(double) * Q);
+  if (oracle_quad_rule(m, X, W) < 0) {
+    free(X);
+    free(W);
+    return -2;
+  }
+  double *B = (double *)malloc(sizeof(double) * Q * n);
+  double *dB = (double *)malloc(sizeof(double) * Q * n * 3);
+  oracle_bernstein_basis(p, Q, X, B, dB);
+  int bad = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(+ : bad)
+#endif
+  for (int64_t e = 0; e < E; ++e) {
+    const double *x = coords + 12 * e;
+    double *A = out + (size_t)n * n * e;
+    double J[3][3], Jinv[3][3];
+    const double det = geometry(x, J, Jinv);
+    if (!(det != 0.0)) bad += 1;
+    const double adet = fabs(det);
+    for (int i = 0; i < n * n; ++i) A[i] = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      const double *b = B + (size_t)q * n;
+      const double *db = dB + (size_t)q * n * 3;
+      const double wq = W[q] * adet;
+      double fq = 1.0;
+      if (form == OR_HELMHOLTZ) {
+        fq = 0.0;
+        for (int k = 0; k < n; ++k) fq += c[(size_t)n * e + k] * b[k];
+      }
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          double v = fq * b[i] * b[j];
+          if (form == OR_HELMHOLTZ) {
+            double gi[3], gj[3];
+            phys_grad(Jinv, db + 3 * i, gi);
+            phys_grad(Jinv, db + 3 * j, gj);
+            v += gi[0] * gj[0] + gi[1] * gj[1] + gi[2] * gj[2];
+          }
+          A[i * n + j] += wq * v;
+        }
+    }
+  }
+  free(X);
+  free(W);
+  free(B);
+  free(dB);
+  return bad;
 }
 
 int oracle_max_threads(void) {

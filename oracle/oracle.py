@@ -55,6 +55,10 @@ def _load():
             lib.oracle_basis.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D]
             lib.oracle_nodes.argtypes = [ctypes.c_int, D]
             lib.oracle_local_dim.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.oracle_bernstein_indices.argtypes = [ctypes.c_int, I]
+            lib.oracle_bernstein_basis.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D]
+            lib.oracle_assemble_bernstein.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, D, D,
+                                                      D, ctypes.c_int]
             lib.oracle_assemble.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, D, D,
                                             ctypes.c_double, ctypes.c_double, D, ctypes.c_int]
             lib.oracle_neohookean_residual.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, D, D,
@@ -185,6 +189,44 @@ def neohookean_energy(p, coords, u, mu=0.8, lam=1.3, m=None):
         m = default_rule(NEOHOOKEAN, p)
     out = np.zeros(E)
     lib.oracle_neohookean_energy(p, m, E, _ptr(coords), _ptr(u), float(mu), float(lam), _ptr(out))
+    return out
+
+
+def bernstein_indices(p):
+    """Multi-indices (a0, a1, a2, a3), |a| = p, of the Bernstein basis in its DOF order [n, 4]."""
+    n = nbasis(p)
+    a = np.zeros((n, 4), dtype=np.int32)
+    _load().oracle_bernstein_indices(p, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return a
+
+
+def bernstein_basis(p, X):
+    """(B [Q,n], dB/dX [Q,n,3]) of the degree-p Bernstein basis at points X [Q,3]."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    Q = X.shape[0]
+    n = nbasis(p)
+    B = np.zeros((Q, n))
+    dB = np.zeros((Q, n, 3))
+    _load().oracle_bernstein_basis(p, Q, _ptr(X), _ptr(B), _ptr(dB))
+    return B, dB
+
+
+def assemble_bernstein(form, p, coords, c=None, m=None, nthreads=1):
+    """Mass or Helmholtz element matrices [E, n, n] in the Bernstein basis; c [E, n]
+    holds the Bernstein coefficients of f (Helmholtz)."""
+    lib = _load()
+    coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1, 12)
+    E = coords.shape[0]
+    n = nbasis(p)
+    if m is None:
+        m = default_rule(HELMHOLTZ, p)
+    cptr = None
+    if form == HELMHOLTZ:
+        c = np.ascontiguousarray(c, dtype=np.float64).reshape(E, n)
+        cptr = _ptr(c)
+    out = np.zeros((E, n, n))
+    if lib.oracle_assemble_bernstein(form, p, m, E, _ptr(coords), cptr, _ptr(out), int(nthreads)) < 0:
+        raise ValueError("oracle_assemble_bernstein rejected form=%d p=%d" % (form, p))
     return out
 
 

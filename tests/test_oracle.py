@@ -412,3 +412,64 @@ def test_neohookean_residual_invariants(orc, p):
         lin = eps * np.einsum("eij,ej->ei", Kl, u)
         errs.append(np.linalg.norm(orc.neohookean_residual(p, c, eps * u) - lin) / np.linalg.norm(lin))
     assert errs[1] < 0.2 * errs[0] and errs[1] < 1e-2
+
+
+# ------------------------------------------------- Bernstein basis (sum factorisation)
+def _bern_elements(p, E, seed):
+    coords, _ = inputs.workload(inputs.MASS, p, E, seed=seed)
+    c = np.random.default_rng(seed).uniform(-1.0, 1.0, (E, inputs.nbasis(p)))
+    return coords, c
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_bernstein_basis_unity_and_gradient_fd(orc, p):
+    rng = np.random.default_rng(10 + p)
+    X = rng.dirichlet(np.ones(4), 20)[:, 1:]
+    B, dB = orc.bernstein_basis(p, X)
+    assert np.allclose(B.sum(axis=1), 1.0, atol=1e-14)
+    assert np.allclose(dB.sum(axis=1), 0.0, atol=1e-12)
+    assert (B >= 0).all()
+    h = 1e-6
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = (orc.bernstein_basis(p, X + e)[0] - orc.bernstein_basis(p, X - e)[0]) / (2 * h)
+        assert np.allclose(fd, dB[:, :, k], atol=1e-7)
+    # vertex values: B_(p e_j) is 1 at vertex j, every other basis function 0
+    al = orc.bernstein_indices(p)
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float)
+    Bv = orc.bernstein_basis(p, V)[0]
+    for j in range(4):
+        k = int(np.where(al[:, j] == p)[0][0])
+        assert abs(Bv[j, k] - 1.0) < 1e-15 and abs(Bv[j].sum() - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_bernstein_mass_closed_form(orc, p):
+    """int_K B_a B_b = |det J| (p!)^2 (a+b)! / (a! b! (2p+3)!) (multi-index factorials)."""
+    coords, _ = _bern_elements(p, 5, 20 + p)
+    A = orc.assemble_bernstein(orc.MASS, p, coords)
+    al = orc.bernstein_indices(p)
+    f = [math.factorial(k) for k in range(2 * p + 4)]
+    for e in range(coords.shape[0]):
+        J = (coords[e, 1:] - coords[e, 0]).T
+        adet = abs(np.linalg.det(J))
+        for i in range(al.shape[0]):
+            for j in range(al.shape[0]):
+                g = al[i] + al[j]
+                num = f[p] ** 2 * np.prod([f[x] for x in g])
+                den = np.prod([f[x] for x in al[i]]) * np.prod([f[x] for x in al[j]]) * f[2 * p + 3]
+                assert abs(A[e, i, j] - adet * num / den) <= 1e-13 * adet
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_bernstein_helmholtz_is_lagrange_helmholtz_in_another_basis(orc, p):
+    """The same space: B_b = sum_i B_b(x_i) phi_i at the Lagrange nodes x_i, so with V[i][b] = B_b(x_i)
+    the Bernstein matrix is V^T A V of the Lagrange matrix for f with Lagrange DOFs V c."""
+    coords, c = _bern_elements(p, 6, 30 + p)
+    V = orc.bernstein_basis(p, orc.nodes(p))[0]
+    AL = orc.assemble(orc.HELMHOLTZ, p, coords, c @ V.T)
+    AB = orc.assemble_bernstein(orc.HELMHOLTZ, p, coords, c)
+    want = np.einsum("ib,eij,jc->ebc", V, AL, V)
+    assert orc.rel_frobenius(AB, want).max() <= 1e-13
+    assert np.abs(AB - AB.transpose(0, 2, 1)).max() <= 1e-13 * np.abs(AB).max()
