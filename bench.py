@@ -305,7 +305,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="helmholtz_p2_1M",
-                    choices=sorted(WORKLOADS) + sorted(VECTOR_WORKLOADS) + ["stream_64req_2M", "helmholtz_p2_global_1M"])
+                    choices=sorted(WORKLOADS) + sorted(VECTOR_WORKLOADS) + ["stream_64req_2M", "helmholtz_p2_global_1M",
+                                                                            "helmholtz_bernstein_p4_200k"])
     ap.add_argument("--elements", type=int, default=0, help="override the element count")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_1604_05872_gb300", "data", "tuning_gb300.json"),
@@ -352,6 +353,8 @@ def main():
         line = run_vector(args, fea, torch, barrier, max_over_ranks, world, rank, local)
     elif args.workload == "helmholtz_p2_global_1M":
         line = run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local)
+    elif args.workload == "helmholtz_bernstein_p4_200k":
+        line = run_bernstein(args, fea, torch, barrier, max_over_ranks, world, rank, local)
     else:
         line = run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local)
     if rank == 0:
@@ -575,6 +578,85 @@ def run_vector(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         line["cpu_baseline"] = {"value": nsamp / dt, "unit": "element vectors/s", "cores": 1, "kind": "oracle",
                                 "sample": "first %d elements, FP64 loop nest, one core, %.2f s" % (nsamp, dt)}
     return line
+
+
+def bernstein_flops(p):
+    """Executed FP32 flops per element of the sum-factorised Bernstein kernel: the
+    six 1-D passes (f at the points, then the moments of degree 2p), the mass
+    entries (one product each) and the six-term pre-evaluated stiffness, 2 flops
+    per multiply-add."""
+    m = (3 * p + 2) // 2
+    n2 = 2 * p
+    ns = (p + 1) * (p + 2) * (p + 3) // 6
+    pairs1 = [(a3, a2) for a3 in range(p + 1) for a2 in range(p - a3 + 1)]
+    e1 = sum(p - a3 - a2 + 1 for a3, a2 in pairs1) * m
+    e2 = sum(p - a3 + 1 for a3 in range(p + 1)) * m * m
+    e3 = m ** 3 * (p + 1) + m ** 3
+    m1 = (n2 + 1) * m * m * m
+    m2 = (n2 + 1) * (n2 + 2) // 2 * m * m
+    m3 = (n2 + 1) * (n2 + 2) * (n2 + 3) // 6 * m
+    return 2 * (e1 + e2 + e3 + m1 + m2 + m3) + ns * ns * (1 + 2 * 6)
+
+
+def run_bernstein(args, fea, torch, barrier, max_over_ranks, world, rank, local):
+    """Helmholtz P4 in the Bernstein-Bezier basis by sum factorisation
+    (fea_assemble_bernstein), 200 000 elements; the Lagrange pre-evaluated
+    kernel on the same elements is timed beside it for comparison."""
+    from paper_1604_05872_gb300 import inputs
+    p, E = 4, args.elements or 200_000
+    coords, _ = inputs.workload(1, p, E, seed=inputs.SEED + rank)
+    ns = (p + 1) * (p + 2) * (p + 3) // 6
+    cb = np.random.Generator(np.random.PCG64(inputs.SEED + 11 + rank)).uniform(-1.0, 1.0, (E, ns))
+    c, fb = torch.from_numpy(coords).cuda(), torch.from_numpy(cb).cuda()
+    f32 = bool(args.out_f32)
+    out = torch.empty((E, ns, ns), dtype=torch.float32 if f32 else torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        fea.sync()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        barrier()
+        fea.sync()
+        return ev0.elapsed_time(ev1) / steps
+
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: fea.assemble_bernstein(1, p, c, fb, out=out, out_f32=f32), args.steps)
+    ms_lagrange = timed(lambda: fea.assemble(1, p, c, fb, out=out, out_f32=f32), max(3, args.steps // 4))
+    ms_max = max_over_ranks(ms)
+    esz = 4 if f32 else 8
+    alg_bytes = E * (96 + 8 * ns + esz * ns * ns)
+    flops = E * bernstein_flops(p)
+    hbm, peak_kind = peaks()
+    t_hbm, t_f32 = alg_bytes / (hbm * 1e9), flops / (FP32_PEAK_TFLOPS * 1e12)
+    if t_hbm >= t_f32:
+        roof = {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_kind": peak_kind}
+    else:
+        roof = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_kind": "derived: FP32 lanes x clock"}
+    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": None, "alg_bytes_per_launch": alg_bytes,
+                 "bound_times_ms": {"hbm": t_hbm * 1e3, "fp32": t_f32 * 1e3}})
+    pl = fea.plan(1, p)
+    return {
+        "metric": METRIC, "value": E * world / (ms_max * 1e-3), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "form": "helmholtz", "degree": p, "elements": E,
+                   "basis": "Bernstein-Bezier", "method": "sum factorisation of the moments of f over the collapsed rule",
+                   "local_matrix": "%dx%d %s" % (ns, ns, "f32" if f32 else "f64"),
+                   "flops_per_element": bernstein_flops(p), "lagrange_pre_flops_per_element": pl["flops_run"],
+                   "l2": "inputs+outputs %.0f MB per step > 129 MB L2; no flush" % (alg_bytes / 1e6)},
+        "comparator": {"kernel": "Lagrange basis, pre-evaluated (fea_assemble, same elements)",
+                       "ms_per_step": ms_lagrange, "value": E / (ms_lagrange * 1e-3), "unit": METRIC},
+        "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(), "e2e": None,
+    }
 
 
 def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):

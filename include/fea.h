@@ -161,6 +161,28 @@ int fea_assemble_host(int form, int degree, int64_t E, const double* coords_host
 int fea_assemble_vector(int form, int degree, int64_t E, const double* coords,
                         const double* coeffs, void* out, const fea_options* opt, void* stream);
 
+/* Helmholtz element matrices in the Bernstein-Bezier basis, computed by sum
+ * factorisation over the collapsed quadrature rule (the paper names sum
+ * factorisation as future work, Section 8 "Limitations and future work"; the
+ * weak form is that of Section 2, the pre-evaluated stiffness that of
+ * Section 3.3).  The same finite element space as FEA_HELMHOLTZ at `degree`
+ * (1..4), in another basis:
+ *   B_a = p!/a! l^a over the multi-indices a = (a0, a1, a2, a3), |a| = p, of the
+ *   barycentric coordinates l0 = 1 - X0 - X1 - X2, l_{k+1} = X_k; DOF order a3
+ *   slowest, then a2, then a1 (a0 = p - a1 - a2 - a3).
+ * coeffs [E][n_p] (DEVICE, doubles): the Bernstein coefficients of f,
+ * f = sum_k c_k B_k; coords as for fea_assemble; out [E][n_p][n_p] (row = test,
+ * column = trial), double, or float with out_f32 = 1.  FP64 geometry, FP32
+ * arithmetic after it (<= 1e-5 relative Frobenius error).  The variable-
+ * coefficient term int f B_a B_b = C(a+b, a) / C(2p, p) int f B^2p_(a+b) takes
+ * the moments of f in six one-dimensional passes (O(p^4) per element instead
+ * of n_p^3).  Asynchronous on `stream`; FEA_EINVAL for another form or
+ * degree, a negative E or host pointers; degenerate elements give NaN and
+ * FEA_EDEGENERATE at the next fea_sync.  The library keeps one table per
+ * degree, freed by fea_finalize. */
+int fea_assemble_bernstein(int form, int degree, int64_t E, const double* coords, const double* coeffs,
+                           void* out, int out_f32, void* stream);
+
 /* The natural logarithm the Neo-Hookean kernels evaluate ln det F with (FP64
  * arithmetic, table-driven: Tang, ACM TOMS 16(4), 1990; 13 FP64 operations),
  * applied to n doubles: y[i] = ln x[i] (DEVICE arrays, on `stream`).  A few

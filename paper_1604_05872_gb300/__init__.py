@@ -78,6 +78,7 @@ def load(path=None):
     lib.fea_coeffs_size.restype = i64
     lib.fea_quad_points.argtypes = [i, i]
     lib.fea_assemble.argtypes = [i, i, i64, vp, vp, vp, vp]
+    lib.fea_assemble_bernstein.argtypes = [i, i, i64, vp, vp, vp, i, vp]
     lib.fea_assemble_ex.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_host.argtypes = [i, i, i64, vp, vp, vp, P(Options), vp]
     lib.fea_assemble_batch.argtypes = [P(Request), i, P(Options), vp]
@@ -206,6 +207,21 @@ def assemble_vector(form, degree, coords, coeffs, out=None, precision=PREC_FP32,
     o = options(precision, out_f32, VARIANT_AUTO, tile, smem_budget)
     _check(load().fea_assemble_vector(form, degree, E, _ptr(coords), _ptr(coeffs), _ptr(out), ctypes.byref(o),
                                       _stream_ptr(stream)))
+    return out
+
+
+def assemble_bernstein(form, degree, coords, coeffs, out=None, out_f32=False, stream=None):
+    """Helmholtz element matrices [E, n_p, n_p] in the Bernstein-Bezier basis by sum
+    factorisation (fea_assemble_bernstein); coeffs [E, n_p]: Bernstein coefficients of f."""
+    import torch
+    E = coords.shape[0]
+    n = local_dim(form, degree)
+    if n < 0:
+        raise FeaError(1, "unsupported form/degree")
+    if out is None:
+        out = torch.empty((E, n, n), dtype=torch.float32 if out_f32 else torch.float64, device=coords.device)
+    _check(load().fea_assemble_bernstein(form, degree, E, _ptr(coords), _ptr(coeffs), _ptr(out), int(bool(out_f32)),
+                                         _stream_ptr(stream)))
     return out
 
 

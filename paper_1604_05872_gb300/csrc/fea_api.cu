@@ -22,6 +22,7 @@
 namespace fea {
 
 bool tc_table_words(int form, int p, std::vector<uint32_t>* words);
+bool bernstein_table_words(int form, int p, std::vector<uint32_t>* words);
 const KernelInfo* find_tc_kernel(int form, int p);
 
 static thread_local std::string g_last_error;
@@ -100,9 +101,11 @@ int get_tables(DevState* st, int form, int p, int prec, TableEntry** out) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto key = std::make_tuple(form, p, prec);
   auto it = st->tables.find(key);
-  if (it == st->tables.end() && prec == 2) {
+  if (it == st->tables.end() && (prec == 2 || prec == 3)) {
+    // 32-bit word tables: the tensor-core kernels (2) and the Bernstein variant (3)
     std::vector<uint32_t> words;
-    if (!tc_table_words(form, p, &words)) return fail(FEA_EINVAL, "no tensor-core table for this form/degree");
+    if (prec == 2 && !tc_table_words(form, p, &words)) return fail(FEA_EINVAL, "no tensor-core table for this form/degree");
+    if (prec == 3 && !bernstein_table_words(form, p, &words)) return fail(FEA_EINVAL, "no Bernstein table for this form/degree");
     TableEntry te;
     te.lay.total = (int)words.size();
     const size_t bytes = words.size() * 4;

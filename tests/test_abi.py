@@ -111,3 +111,15 @@ def test_log_and_pattern_argument_checks_without_gpu(lib):
     assert lib.fea_log_f64(nul, nul, 0, nul) == 0  # nothing to do
     nnz = ctypes.c_int64(0)
     assert lib.fea_csr_pattern(1, 4, nul, 10, 2, nul, nul, ctypes.byref(nnz)) == fea.EINVAL  # upper not 0/1
+
+
+def test_bernstein_argument_checks_on_cpu(lib):
+    """The Bernstein entry point refuses other forms, degrees, negative sizes and bad
+    out_f32 flags before it touches a device."""
+    import paper_1604_05872_gb300 as fea
+    nul = None
+    assert lib.fea_assemble_bernstein(fea.MASS, 2, 10, nul, nul, nul, 0, nul) == fea.EINVAL
+    assert lib.fea_assemble_bernstein(fea.NEOHOOKEAN, 2, 10, nul, nul, nul, 0, nul) == fea.EINVAL
+    assert lib.fea_assemble_bernstein(fea.HELMHOLTZ, 5, 10, nul, nul, nul, 0, nul) == fea.EINVAL
+    assert lib.fea_assemble_bernstein(fea.HELMHOLTZ, 2, -1, nul, nul, nul, 0, nul) == fea.EINVAL
+    assert lib.fea_assemble_bernstein(fea.HELMHOLTZ, 2, 10, nul, nul, nul, 2, nul) == fea.EINVAL
