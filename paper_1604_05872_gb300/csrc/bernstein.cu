@@ -229,63 +229,117 @@ __device__ __forceinline__ void bern_sf_moments(const Req& q, int64_t e, float a
   const float* W = reinterpret_cast<const float*>(sw + C::O_W);
   const int* P1 = reinterpret_cast<const int*>(sw + C::SMALL1);
   const int* P2 = P1 + 3 * C::NP1;
-  const int* MUD = P2 + 3 * C::NP2;
   float* gA = scr;          // g1 [NP1][M], then h2 [NP2][M]
   float* gB = gA + C::SA;   // g2 [P+1][M M], then h1 [N2+1][M M]
   float* F = gB + C::SB;    // w |det J| f at the points [Q]
   float* c = F + C::Q + C::EW * C::NM;  // Bernstein coefficients of f [NS]
   for (int i = lane; i < C::NS; i += 32) c[i] = d2f(q.coeffs[e * C::NS + i]);
   __syncwarp();
-  // f at (r_i, s_j, t_k): over a1 (t), then a2 (s), then a3 (r)
-  for (int o = lane; o < C::NP1 * M; o += 32) {
-    const int pr = o / M, k = o - pr * M;
+  // Each pass is a small product: a lane takes one column of its output and keeps
+  // the column's entries (one per value of the short index) in registers.
+  // f at (r_i, s_j, t_k): over a1 (t), column (a3, a2), entries k
+  for (int pr = lane; pr < C::NP1; pr += 32) {
     const int d = P - P1[3 * pr] - P1[3 * pr + 1], base = P1[3 * pr + 2];
-    float acc = 0.f;
-    for (int a1 = 0; a1 <= d; ++a1) acc = fmaf(Tt[C::row1(d, a1) * M + k], c[base + a1], acc);
-    gA[o] = acc;
+    float acc[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int a1 = 0; a1 <= P; ++a1)
+      if (a1 <= d) {
+        const float cv = c[base + a1];
+        const float* tr = Tt + C::row1(d, a1) * M;
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[k] = fmaf(tr[k], cv, acc[k]);
+      }
+#pragma unroll
+    for (int k = 0; k < M; ++k) gA[pr * M + k] = acc[k];
   }
   __syncwarp();
-  for (int o = lane; o < (P + 1) * MM; o += 32) {
-    const int a3 = o / MM, jk = o - a3 * MM, j = jk / M, k = jk - j * M, d = P - a3;
+  // over a2 (s): column (a3, k), entries j
+  for (int col = lane; col < (P + 1) * M; col += 32) {
+    const int a3 = col / M, k = col - a3 * M, d = P - a3;
     const int pb = a3 * (P + 1) - a3 * (a3 - 1) / 2;  // pairs (a3', a2) with a3' < a3
-    float acc = 0.f;
-    for (int a2 = 0; a2 <= d; ++a2) acc = fmaf(Ts[C::row1(d, a2) * M + j], gA[(pb + a2) * M + k], acc);
-    gB[o] = acc;
+    float acc[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int a2 = 0; a2 <= P; ++a2)
+      if (a2 <= d) {
+        const float g = gA[(pb + a2) * M + k];
+        const float* tr = Ts + C::row1(d, a2) * M;
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[j] = fmaf(tr[j], g, acc[j]);
+      }
+#pragma unroll
+    for (int j = 0; j < M; ++j) gB[a3 * MM + j * M + k] = acc[j];
   }
   __syncwarp();
-  for (int o = lane; o < C::Q; o += 32) {
-    const int i = o / MM, jk = o - i * MM;
-    float acc = 0.f;
+  // over a3 (r): column (j, k), entries i; then w |det J| f
+  for (int col = lane; col < MM; col += 32) {
+    float acc[M];
 #pragma unroll
-    for (int a3 = 0; a3 <= P; ++a3) acc = fmaf(Tr[C::row1(P, a3) * M + i], gB[a3 * MM + jk], acc);
-    F[o] = W[o] * adet * acc;
+    for (int i = 0; i < M; ++i) acc[i] = 0.f;
+#pragma unroll
+    for (int a3 = 0; a3 <= P; ++a3) {
+      const float g = gB[a3 * MM + col];
+      const float* tr = Tr + C::row1(P, a3) * M;
+#pragma unroll
+      for (int i = 0; i < M; ++i) acc[i] = fmaf(tr[i], g, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) F[i * MM + col] = W[i * MM + col] * adet * acc[i];
   }
   __syncwarp();
-  // moments mu_g = sum_q F_q B^2p_g(X_q): over r (g3), then s (g2), then t (g1)
-  for (int o = lane; o < (C::N2 + 1) * MM; o += 32) {
-    const int g3 = o / MM, jk = o - g3 * MM;
-    float acc = 0.f;
+  // moments mu_g = sum_q F_q B^2p_g(X_q): over r, column (j, k), entries g3
+  for (int col = lane; col < MM; col += 32) {
+    float acc[C::N2 + 1];
 #pragma unroll
-    for (int i = 0; i < M; ++i) acc = fmaf(Tr[C::row1(C::N2, g3) * M + i], F[i * MM + jk], acc);
-    gB[o] = acc;
+    for (int g3 = 0; g3 <= C::N2; ++g3) acc[g3] = 0.f;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const float f = F[i * MM + col];
+#pragma unroll
+      for (int g3 = 0; g3 <= C::N2; ++g3) acc[g3] = fmaf(Tr[C::row1(C::N2, g3) * M + i], f, acc[g3]);
+    }
+#pragma unroll
+    for (int g3 = 0; g3 <= C::N2; ++g3) gB[g3 * MM + col] = acc[g3];
   }
   __syncwarp();
-  for (int o = lane; o < C::NP2 * M; o += 32) {
-    const int pr = o / M, k = o - pr * M;
-    const int g3 = P2[3 * pr], g2 = P2[3 * pr + 1], d = C::N2 - g3;
-    float acc = 0.f;
+  // over s: column (g3, k), entries g2 <= 2p - g3
+  for (int col = lane; col < (C::N2 + 1) * M; col += 32) {
+    const int g3 = col / M, k = col - g3 * M, d = C::N2 - g3;
+    const int pb = g3 * (C::N2 + 1) - g3 * (g3 - 1) / 2;  // pairs (g3', g2) with g3' < g3
+    float acc[C::N2 + 1];
 #pragma unroll
-    for (int j = 0; j < M; ++j) acc = fmaf(Ts[C::row1(d, g2) * M + j], gB[g3 * MM + j * M + k], acc);
-    gA[o] = acc;
+    for (int g2 = 0; g2 <= C::N2; ++g2) acc[g2] = 0.f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float h = gB[g3 * MM + j * M + k];
+#pragma unroll
+      for (int g2 = 0; g2 <= C::N2; ++g2)
+        if (g2 <= d) acc[g2] = fmaf(Ts[C::row1(d, g2) * M + j], h, acc[g2]);
+    }
+#pragma unroll
+    for (int g2 = 0; g2 <= C::N2; ++g2)
+      if (g2 <= d) gA[(pb + g2) * M + k] = acc[g2];
   }
   __syncwarp();
-  for (int o = lane; o < C::NM; o += 32) {
-    const int pr = MUD[2 * o], g1 = MUD[2 * o + 1];
-    const int d = C::N2 - P2[3 * pr] - P2[3 * pr + 1];
-    float acc = 0.f;
+  // over t: column (g3, g2), entries g1 <= 2p - g3 - g2
+  for (int pr = lane; pr < C::NP2; pr += 32) {
+    const int d = C::N2 - P2[3 * pr] - P2[3 * pr + 1], base = P2[3 * pr + 2];
+    float acc[C::N2 + 1];
 #pragma unroll
-    for (int k = 0; k < M; ++k) acc = fmaf(Tt[C::row1(d, g1) * M + k], gA[pr * M + k], acc);
-    mu[o] = acc;
+    for (int g1 = 0; g1 <= C::N2; ++g1) acc[g1] = 0.f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const float h = gA[pr * M + k];
+#pragma unroll
+      for (int g1 = 0; g1 <= C::N2; ++g1)
+        if (g1 <= d) acc[g1] = fmaf(Tt[C::row1(d, g1) * M + k], h, acc[g1]);
+    }
+#pragma unroll
+    for (int g1 = 0; g1 <= C::N2; ++g1)
+      if (g1 <= d) mu[base + g1] = acc[g1];
   }
   __syncwarp();
 }
