@@ -59,7 +59,8 @@ PROFILES = {
     "neohookean_p3_100k@bf16x2": ("neohookean_p3_tc_100k.md",
                                   ["common.cuh", "layout.h", "launch.cuh", "mbar.cuh", "tc.cuh", "nh_tce.cuh",
                                    "log_f64.cuh", "log_table.h", "kernels_tc.cu"]),
-    "helmholtz_p2_global_1M": ("global_helmholtz_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh", "planner.cpp"]),
+    "helmholtz_p2_global_1M": ("global_helmholtz_p2_1M.md",
+                               ["common.cuh", "layout.h", "kernels.h", "pre_stream.cuh", "pre_combine.cuh", "planner.cpp"]),
     "helmholtz_load_p2_1M": ("helmholtz_load_p2_1M.md", ["common.cuh", "layout.h", "pre_stream.cuh"]),
     "neohookean_residual_p2_500k": ("neohookean_residual_p2_500k.md",
                                     ["common.cuh", "layout.h", "launch.cuh", "vec_forms.cuh", "log_f64.cuh",
@@ -662,9 +663,11 @@ def run_bernstein(args, fea, torch, barrier, max_over_ranks, world, rank, local)
 def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     """Local and global assembly together (the paper times them jointly): Helmholtz P2 on a
     conforming mesh of the unit cube (55^3 cubes x 6 tetrahedra = 998 250 elements, 1.37 M DOFs).
-    One step: zero the CSR values, then fea_assemble_csr (element matrices added into the CSR
-    values at positions computed once per mesh, never stored).  Also timed: the two-pass form
-    (fea_assemble, then fea_scatter_add_csr_mapped) and the scatters alone."""
+    One step: zero the CSR values, then fea_assemble_csr_combined (element matrices summed per
+    distinct CSR position of a tile in shared memory, one FP64 atomic per position, never
+    stored; the positions and their grouping computed once per mesh).  Also timed: the one-pass
+    kernel with one atomic per entry (fea_assemble_csr), the two-pass form (fea_assemble, then
+    fea_scatter_add_csr_mapped), the scatters alone and symmetric storage."""
     from paper_1604_05872_gb300 import inputs
     coords, dofs, nd = inputs.box_mesh(55, 2, jitter=0.1, seed=inputs.SEED + rank)
     E = coords.shape[0]
@@ -676,11 +679,24 @@ def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     c, fc = torch.from_numpy(coords).cuda(), torch.from_numpy(inputs.coeff_array(1, 2, f)).cuda()
     dd, rp, ci = (torch.from_numpy(x).cuda() for x in (dofs, row_ptr, col_idx))
     elem = fea.empty_out(1, 2, E)
-    vals = torch.zeros(col_idx.shape[0], dtype=torch.float64, device="cuda")
+    nnz = col_idx.shape[0]
+    vals = torch.zeros(nnz, dtype=torch.float64, device="cuda")
     smap = fea.csr_scatter_map(dd, rp, ci)  # CSR positions, once per mesh
+    t0 = time.perf_counter()
+    host_plan = fea.csr_combine_plan(smap, nnz)  # grouping per tile, once per mesh
+    t_plan = time.perf_counter() - t0
+    plan = torch.from_numpy(host_plan).cuda()
+    tile = int(host_plan[2])
+    ntiles = (E + tile - 1) // tile
+    toff = host_plan[4:4 + 2 * (ntiles + 1)].view(np.int64)
+    positions = int(host_plan[toff[:-1]].astype(np.int64).sum())  # one FP64 atomic each
     stream = torch.cuda.current_stream()
 
     def step():
+        vals.zero_()
+        fea.assemble_csr_combined(1, 2, c, fc, plan, vals)
+
+    def one_pass_map():
         vals.zero_()
         fea.assemble_csr(1, 2, c, fc, smap, vals)
 
@@ -700,6 +716,7 @@ def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):
 
     for _ in range(args.warmup):
         step()
+        one_pass_map()
         two_pass()
     fea.sync()
     barrier()
@@ -711,40 +728,52 @@ def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         ev[1].record(stream)
         barrier()
     ms = ev[0].elapsed_time(ev[1]) / args.steps
-    # the one-pass kernel alone (it accumulates: the same work every launch), the two-pass step,
-    # and its scatter with precomputed positions and with the per-entry search
-    ms_kernel = timed(lambda: fea.assemble_csr(1, 2, c, fc, smap, vals), args.steps)
+    # the combined kernel alone (it accumulates: the same work every launch), the one-pass step
+    # with one atomic per entry and its kernel, the two-pass step, and its scatter with
+    # precomputed positions and with the per-entry search
+    ms_kernel = timed(lambda: fea.assemble_csr_combined(1, 2, c, fc, plan, vals), args.steps)
+    ms_map_kernel = timed(lambda: fea.assemble_csr(1, 2, c, fc, smap, vals), args.steps)
+    ms_map = timed(one_pass_map, args.steps)
     ms_two = timed(two_pass, args.steps)
     # symmetric storage: the upper triangle only (55 of the 100 entries of each element matrix)
     ur, uc = fea.csr_pattern(dofs, nd, upper=True)
     umap = fea.csr_scatter_map(dd, torch.from_numpy(ur).cuda(), torch.from_numpy(uc).cuda(), upper=True)
+    uplan = torch.from_numpy(fea.csr_combine_plan(umap, uc.shape[0])).cuda()
     uvals = torch.zeros(uc.shape[0], dtype=torch.float64, device="cuda")
 
     def sym_step():
+        uvals.zero_()
+        fea.assemble_csr_combined(1, 2, c, fc, uplan, uvals)
+
+    def sym_map_step():
         uvals.zero_()
         fea.assemble_csr(1, 2, c, fc, umap, uvals)
 
     for _ in range(args.warmup):
         sym_step()
+        sym_map_step()
     ms_sym = timed(sym_step, args.steps)
+    ms_sym_map = timed(sym_map_step, args.steps)
     ms_scatter = timed(lambda: fea.scatter_add_csr_mapped(smap, elem, vals), args.steps)
     ms_search = timed(lambda: fea.scatter_add_csr(dd, elem, rp, ci, vals), max(1, args.steps // 4))
     fea.sync()
     ms_max = max_over_ranks(ms)
-    nnz = col_idx.shape[0]
-    # algorithmic bytes of the one-pass kernel: coordinates and coefficients (176 B/element), the
-    # position map (100 entries per element), one read and one write of every CSR value; the step
-    # adds the zeroing of the values (8 B per entry)
-    map_bytes = 100 * smap.element_size()
-    kernel_bytes = E * (176 + map_bytes) + nnz * 16
+    # algorithmic bytes of the combined kernel: coordinates and coefficients (176 B/element), the
+    # plan (positions, tile-entry indices, headers), one read and one write of every CSR value;
+    # the step adds the zeroing of the values (8 B per entry)
+    plan_bytes = 4 * host_plan.shape[0]
+    kernel_bytes = E * 176 + plan_bytes + nnz * 16
     step_bytes = kernel_bytes + nnz * 8
+    map_kernel_bytes = E * (176 + 100 * smap.element_size()) + nnz * 16
     hbm, peak_kind = peaks()
-    roof = {"bound": "hbm", "kernel": "pre_stream_scatter_kernel<1, 2, %d>" % smap.element_size(),
+    roof = {"bound": "hbm", "kernel": "pre_combine_kernel<1, 2>",
             "achieved": kernel_bytes / (ms_kernel * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
             "peak_kind": peak_kind, "traffic": profiled_traffic(args.workload),
             "alg_bytes_per_launch": kernel_bytes, "kernel_ms": ms_kernel,
-            "fp64_atomics_per_s": E * 100 / (ms_kernel * 1e-3),
-            "step_achieved": step_bytes / (ms * 1e-3) / 1e9, "step_alg_bytes": step_bytes}
+            "fp64_atomics_per_launch": positions, "fp64_atomics_per_s": positions / (ms_kernel * 1e-3),
+            "step_achieved": step_bytes / (ms * 1e-3) / 1e9, "step_alg_bytes": step_bytes,
+            "map_kernel_ms": ms_map_kernel,
+            "map_kernel_frac": map_kernel_bytes / (ms_map_kernel * 1e-3) / 1e9 / hbm}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["step_frac"] = roof["step_achieved"] / roof["peak"]
     line = {
@@ -753,10 +782,14 @@ def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "form": "helmholtz", "degree": 2, "elements": E, "dofs": nd,
                    "nnz": nnz, "local_matrix": "10x10, never stored",
-                   "global": "CSR f64, FP64 atomics at precomputed positions (%s map)" % str(smap.dtype).replace("torch.", ""),
-                   "two_pass_ms": ms_two, "scatter_ms": ms_scatter, "scatter_with_search_ms": ms_search,
-                   "symmetric_storage_ms": ms_sym, "symmetric_nnz": int(uc.shape[0]),
-                   "pattern_host_s": t_pattern,
+                   "global": "CSR f64; a tile's entries summed per distinct position in shared memory, one "
+                             "FP64 atomic per position (%d tiles of %d elements, %.1f atomics per element)"
+                             % (ntiles, tile, positions / E),
+                   "plan_bytes": plan_bytes, "plan_host_s": t_plan, "pattern_host_s": t_pattern,
+                   "one_pass_map_ms": ms_map, "two_pass_ms": ms_two, "scatter_ms": ms_scatter,
+                   "scatter_with_search_ms": ms_search,
+                   "symmetric_storage_ms": ms_sym, "symmetric_storage_map_ms": ms_sym_map,
+                   "symmetric_nnz": int(uc.shape[0]),
                    "l2": "%.0f MB per step > 129 MB L2; no flush" % (step_bytes / 1e6)},
         "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(), "e2e": None,
     }

@@ -246,6 +246,40 @@ int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, c
 int fea_assemble_csr(int form, int degree, int64_t E, const double* coords, const double* coeffs,
                      const void* map, int map_i64, int64_t nnz, double* values, void* stream);
 
+/* Combining plan of the one-pass global assembly (HOST arrays, no GPU needed),
+ * computed once per mesh from the position map of fea_csr_scatter_map (copied
+ * to the host; [E][n][n], int32 when map_i64 = 0, else int64): for every tile of
+ * T = min(256, 12800 / n^2 rounded down to even) consecutive elements, the
+ * distinct CSR positions the tile's entries fall on and, per position, which of
+ * the tile's entries add to it (Section 2: the global matrix is the sum of the
+ * element matrices at their global DOFs; entries of one tile meeting at one
+ * position are summed before they reach the global values).  Layout (32-bit
+ * words, documented in csrc/pre_combine.cuh): a header (magic, n, T), int64
+ * offsets of the tile records, then per tile the number of distinct positions,
+ * the positions ordered by how many entries meet there (largest first) and the
+ * 16-bit tile-local entry indices round by round.  Map entries -2 (lower
+ * triangle under symmetric storage) are left out.  Call with plan = NULL to get
+ * the size in *plan_words, then with a buffer of that many words; the call
+ * writes the size used into *plan_words.  FEA_EINVAL: a position outside
+ * [0, nnz) other than -2, nnz >= 2^31, n^2 T > 65536, or a buffer smaller than
+ * needed. */
+int fea_csr_combine_plan(int64_t E, int n, const void* map, int map_i64, int64_t nnz, int32_t* plan,
+                         int64_t* plan_words);
+
+/* fea_assemble_csr with the plan above (DEVICE copy, 16-byte aligned,
+ * plan_words 32-bit words) in place of the map: the element entries of a tile
+ * are staged in shared memory, every distinct position of the tile is summed
+ * from them in FP64 (each FP32 entry widened exactly) and added to values [nnz]
+ * with one FP64 atomic.  The result equals the two-pass assembly's up to the
+ * order of the FP64 additions.  Mass and Helmholtz P1-P3 (FEA_EINVAL for
+ * others, or a plan too short for E elements or not 16-byte aligned).  A plan
+ * that is not for this local dimension and tile size, or breaks a bound of its
+ * layout, is flagged: the next fea_sync returns FEA_EINVAL and the offending
+ * tiles or positions are skipped; a degenerate element adds NaN and makes it
+ * return FEA_EDEGENERATE. */
+int fea_assemble_csr_combined(int form, int degree, int64_t E, const double* coords, const double* coeffs,
+                              const int32_t* plan, int64_t plan_words, int64_t nnz, double* values, void* stream);
+
 /* Uneven batch of requests (forms, degrees and sizes mixed) in one CUDA graph
  * launch, captured once per distinct batch and replayed: each request runs the
  * persistent kernel it would run alone (its own tile, registers and shared

@@ -24,7 +24,8 @@ VARIANT_NAMES = {VARIANT_NAIVE: "naive", VARIANT_SE: "se", VARIANT_PRE: "pre"}
 
 EXPORTS = ["fea_local_dim", "fea_coeff_len", "fea_coeffs_size", "fea_quad_points", "fea_assemble",
            "fea_assemble_vector", "fea_csr_pattern", "fea_scatter_add_csr",
-           "fea_csr_scatter_map", "fea_scatter_add_csr_mapped", "fea_assemble_csr", "fea_log_f64",
+           "fea_csr_scatter_map", "fea_scatter_add_csr_mapped", "fea_assemble_csr", "fea_csr_combine_plan",
+           "fea_assemble_csr_combined", "fea_log_f64",
            "fea_assemble_ex", "fea_assemble_host", "fea_assemble_batch", "fea_assemble_batch_fused",
            "fea_assemble_batch_noalloc",
            "fea_sync", "fea_test_skip_input_copy", "fea_plan", "fea_plan_flop",
@@ -89,6 +90,8 @@ def load(path=None):
     lib.fea_csr_scatter_map.argtypes = [i64, i, vp, i64, vp, vp, i64, i, vp, i, vp]
     lib.fea_log_f64.argtypes = [vp, vp, i64, vp]
     lib.fea_assemble_csr.argtypes = [i, i, i64, vp, vp, vp, i, i64, vp, vp]
+    lib.fea_csr_combine_plan.argtypes = [i64, i, vp, i, i64, vp, P(i64)]
+    lib.fea_assemble_csr_combined.argtypes = [i, i, i64, vp, vp, vp, i64, i64, vp, vp]
     lib.fea_scatter_add_csr_mapped.argtypes = [i64, i, vp, i, vp, i, i64, vp, vp]
     lib.fea_assemble_batch_noalloc.argtypes = [P(Request), i, P(Options), vp]
     lib.fea_sync.argtypes = [vp]
@@ -278,6 +281,38 @@ def assemble_csr(form, degree, coords, coeffs, scatter_map, values, stream=None)
     _check(load().fea_assemble_csr(form, degree, coords.shape[0], _ptr(coords), _ptr(coeffs),
                                    _ptr(scatter_map), int(scatter_map.dtype == torch.int64), values.shape[0],
                                    _ptr(values), _stream_ptr(stream)))
+    return values
+
+
+def csr_combine_plan(scatter_map, nnz):
+    """Combining plan of the one-pass global assembly (int32 words, numpy) from a position map
+    [E, n, n] (int32 or int64; numpy, or a tensor, copied to the host); fea_csr_combine_plan.
+    For every tile of elements: the distinct CSR positions its entries fall on and which
+    entries meet at each."""
+    import numpy as np
+    m = scatter_map.cpu().numpy() if hasattr(scatter_map, "cpu") else scatter_map
+    if m.dtype not in (np.int32, np.int64) or m.ndim != 3 or m.shape[1] != m.shape[2]:
+        raise TypeError("scatter map must be an int32 or int64 array [E, n, n]")
+    m = np.ascontiguousarray(m)
+    E, n = m.shape[0], m.shape[1]
+    words = ctypes.c_int64(0)
+    lib = load()
+    _check(lib.fea_csr_combine_plan(E, n, m.ctypes.data, int(m.dtype == np.int64), nnz, None, ctypes.byref(words)))
+    plan = np.zeros(words.value, dtype=np.int32)
+    _check(lib.fea_csr_combine_plan(E, n, m.ctypes.data, int(m.dtype == np.int64), nnz, plan.ctypes.data,
+                                    ctypes.byref(words)))
+    return plan[:words.value]
+
+
+def assemble_csr_combined(form, degree, coords, coeffs, plan, values, stream=None):
+    """fea_assemble_csr with a tile's entries combined per CSR position before the FP64 atomics:
+    values += the global matrix (mass, Helmholtz P1-P3); `plan` is the device copy (int32 tensor)
+    of csr_combine_plan.  Returns `values`."""
+    import torch
+    if plan.dtype != torch.int32:
+        raise TypeError("plan must be int32")
+    _check(load().fea_assemble_csr_combined(form, degree, coords.shape[0], _ptr(coords), _ptr(coeffs), _ptr(plan),
+                                            plan.numel(), values.shape[0], _ptr(values), _stream_ptr(stream)))
     return values
 
 

@@ -454,6 +454,63 @@ int assemble_csr_impl(int form, int degree, int64_t E, const double* coords, con
   return FEA_OK;
 }
 
+// The same with the entries of each tile combined per CSR position (plan from
+// fea_csr_combine_plan): one FP64 atomic per distinct position of a tile.
+int assemble_csr_combined_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs,
+                               const int32_t* plan, int64_t plan_words, int64_t nnz, double* values, void* stream) {
+  if (!valid_fd(form, degree)) return fail(FEA_EINVAL, "unsupported form/degree");
+  size_t smem = 0;
+  const void* fn = find_combine_kernel(form, degree, &smem);
+  if (!fn) return fail(FEA_EINVAL, "combined global assembly covers mass and Helmholtz P1-P3");
+  if (E < 0 || nnz < 0 || plan_words < 0) return fail(FEA_EINVAL, "negative size");
+  const int n = local_dim(form, degree);
+  if (E > (int64_t)(INT64_MAX / ((int64_t)n * n * 8))) return fail(FEA_EINVAL, "size overflow");
+  const int T = combine_tile(n);
+  const int64_t ntiles = (E + T - 1) / T;
+  if (plan_words < 4 + 2 * (ntiles + 1)) return fail(FEA_EINVAL, "plan too short for E elements");
+  if (reinterpret_cast<uintptr_t>(plan) % 16) return fail(FEA_EINVAL, "plan must be 16-byte aligned");
+  DevState* st = nullptr;
+  int rc = get_dev(&st);
+  if (rc) return rc;
+  fea_options o = default_options();
+  o.variant = FEA_VARIANT_PRE;
+  Plan pl;
+  if ((rc = make_plan(st, form, degree, o, &pl, false))) return rc;
+  if (!find_scatter_kernel(pl.k->fn, 0)) return fail(FEA_EINVAL, "no one-pass kernel for this plan");
+  if (E == 0) return FEA_OK;
+  if ((rc = check_device_ptr(coords, "coords", false))) return rc;
+  if ((rc = check_device_ptr(coeffs, "coeffs", form == FEA_MASS))) return rc;
+  if ((rc = check_device_ptr(plan, "plan", false))) return rc;
+  if ((rc = check_device_ptr(values, "values", nnz == 0))) return rc;
+  PreparedLaunch L;
+  if ((rc = prepare_launch(st, pl, form, degree, E, coords, coeffs, nullptr, 0, &L))) return rc;
+  L.q.tile = T;  // the plan's tile, whatever the planner chose
+  int per_sm = 0;
+  {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> occ;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(fn, st->dev);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+      cudaFuncAttributes fa;
+      CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+      CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)st->smem_optin - (int)fa.sharedSizeBytes));
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem));
+      occ[key] = per_sm;
+    } else {
+      per_sm = it->second;
+    }
+  }
+  if (per_sm < 1) return fail(FEA_EINVAL, "kernel cannot be resident with the combining tile");
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)st->sms * per_sm);
+  CombineArgs cb{plan, plan_words, nnz, values};
+  void* args[] = {&L.q, &cb, &L.err};
+  CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, (cudaStream_t)stream));
+  return FEA_OK;
+}
+
 // Element vectors (linear forms): Helmholtz load vector, Neo-Hookean residual.
 int assemble_vector_impl(int form, int degree, int64_t E, const double* coords, const double* coeffs, void* out,
                          const fea_options* opt, void* stream) {
@@ -643,6 +700,11 @@ int fea_assemble_batch_fused(const fea_request* reqs, int nreq, const fea_option
 int fea_assemble_csr(int form, int degree, int64_t E, const double* coords, const double* coeffs, const void* map,
                      int map_i64, int64_t nnz, double* values, void* stream) {
   return assemble_csr_impl(form, degree, E, coords, coeffs, map, map_i64, nnz, values, stream);
+}
+
+int fea_assemble_csr_combined(int form, int degree, int64_t E, const double* coords, const double* coeffs,
+                              const int32_t* plan, int64_t plan_words, int64_t nnz, double* values, void* stream) {
+  return assemble_csr_combined_impl(form, degree, E, coords, coeffs, plan, plan_words, nnz, values, stream);
 }
 int fea_assemble_batch_noalloc(const fea_request* reqs, int nreq, const fea_options* opt, void* stream) {
   return batch_noalloc_impl(reqs, nreq, opt, stream);

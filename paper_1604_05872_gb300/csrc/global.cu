@@ -16,12 +16,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/fea.h"
 #include "common.cuh"
+#include "kernels.h"
 
 namespace fea {
 
@@ -217,6 +220,110 @@ int scatter_mapped_impl(int64_t E, int n, const void* map, int map_i64, const vo
   return FEA_OK;
 }
 
+// Record of one tile of the combining plan (layout in pre_combine.cuh), or only
+// its size in words when out is null; -1 for a position outside [0, nnz).
+template <typename TM>
+int64_t combine_tile_record(const TM* map, int64_t e0, int ne, int nn, int64_t nnz, std::vector<uint64_t>& keys,
+                            std::vector<int32_t>& slot_start, std::vector<int32_t>& slot_order, int32_t* out) {
+  keys.clear();
+  const TM* m = map + e0 * nn;
+  for (int k = 0; k < ne * nn; ++k) {
+    const int64_t pos = (int64_t)m[k];
+    if (pos == kSkipPos) continue;
+    if (pos < 0 || pos >= nnz) return -1;
+    keys.push_back((uint64_t)pos << 16 | (uint64_t)k);  // k < 2^16: n^2 T <= 65536
+  }
+  std::sort(keys.begin(), keys.end());
+  slot_start.clear();
+  for (size_t i = 0; i < keys.size(); ++i)
+    if (i == 0 || (keys[i] >> 16) != (keys[i - 1] >> 16)) slot_start.push_back((int32_t)i);
+  const int U = (int)slot_start.size(), L = (int)keys.size();
+  slot_start.push_back(L);
+  // positions by number of entries, largest first; ascending position among equals
+  slot_order.resize((size_t)U);
+  for (int s = 0; s < U; ++s) slot_order[(size_t)s] = s;
+  auto mult = [&](int32_t s) { return slot_start[(size_t)s + 1] - slot_start[(size_t)s]; };
+  std::stable_sort(slot_order.begin(), slot_order.end(), [&](int32_t a, int32_t b) { return mult(a) > mult(b); });
+  const int R = U ? mult(slot_order[0]) : 0;
+  const int64_t cw = (R + 3) & ~3, pw = (U + 3) & ~3, iw = ((L + 1) / 2 + 3) & ~3;
+  const int64_t words = 4 + cw + pw + iw;
+  if (!out) return words;
+  std::fill(out, out + words, 0);
+  out[0] = U;
+  out[1] = R;
+  out[2] = L;
+  int32_t* cnt = out + 4;
+  int32_t* pos = cnt + cw;
+  uint16_t* idx = reinterpret_cast<uint16_t*>(pos + pw);
+  for (int s = 0; s < U; ++s) {
+    const int32_t so = slot_order[(size_t)s];
+    pos[s] = (int32_t)(keys[(size_t)slot_start[(size_t)so]] >> 16);
+    for (int r = 0; r < mult(so); ++r) ++cnt[r];  // positions with more than r entries
+  }
+  int64_t off = 0;
+  for (int r = 0; r < R; ++r) {
+    for (int s = 0; s < cnt[r]; ++s)
+      idx[off + s] = (uint16_t)(keys[(size_t)slot_start[(size_t)slot_order[(size_t)s]] + r] & 0xffff);
+    off += cnt[r];
+  }
+  return words;
+}
+
+// The combining plan of a position map (host): tile records built in parallel.
+int csr_combine_plan_impl(int64_t E, int n, const void* map, int map_i64, int64_t nnz, int32_t* plan,
+                          int64_t* plan_words) {
+  if (E < 0 || n < 1 || nnz < 0 || !plan_words) return set_error(FEA_EINVAL, "bad combining-plan arguments");
+  if (map_i64 != 0 && map_i64 != 1) return set_error(FEA_EINVAL, "map_i64 must be 0 or 1");
+  if (E > 0 && !map) return set_error(FEA_EINVAL, "map is null");
+  if (nnz > kMaxMap32) return set_error(FEA_EINVAL, "the plan holds 32-bit positions: nnz must be below 2^31");
+  const int T = combine_tile(n);
+  const int nn = n * n;
+  if ((int64_t)nn * T > 65536) return set_error(FEA_EINVAL, "local dimension too large for 16-bit tile entries");
+  const int64_t ntiles = (E + T - 1) / T;
+  const int64_t hdr = (4 + 2 * (ntiles + 1) + 3) & ~3ll;
+  std::vector<int64_t> off((size_t)ntiles + 1, 0);
+  std::atomic<bool> bad{false};
+  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+  const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), (ntiles + 15) / 16));
+  // pass 1: sizes (out == nullptr); pass 2: the records, into the plan
+  auto run = [&](bool fill) {
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nth; ++w)
+      pool.emplace_back([&, w, fill] {
+        std::vector<uint64_t> keys;
+        std::vector<int32_t> start, order;
+        keys.reserve((size_t)nn * T);
+        for (int64_t t = w; t < ntiles && !bad.load(std::memory_order_relaxed); t += nth) {
+          const int64_t e0 = t * T;
+          const int ne = (int)std::min<int64_t>(T, E - e0);
+          int32_t* out = fill ? plan + off[(size_t)t] : nullptr;
+          const int64_t words =
+              map_i64 ? combine_tile_record(static_cast<const int64_t*>(map), e0, ne, nn, nnz, keys, start, order, out)
+                      : combine_tile_record(static_cast<const int32_t*>(map), e0, ne, nn, nnz, keys, start, order, out);
+          if (words < 0) bad = true;
+          else if (!fill) off[(size_t)t + 1] = words;
+        }
+      });
+    for (auto& th : pool) th.join();
+  };
+  run(false);
+  if (bad) return set_error(FEA_EINVAL, "a map position is outside [0, nnz) (and not -2)");
+  off[0] = hdr;
+  for (int64_t t = 0; t < ntiles; ++t) off[(size_t)t + 1] += off[(size_t)t];
+  const int64_t total = off[(size_t)ntiles];
+  if (plan) {
+    if (*plan_words < total) return set_error(FEA_EINVAL, "plan is smaller than needed (query plan_words first)");
+    std::fill(plan, plan + hdr, 0);
+    plan[0] = kCombineMagic;
+    plan[1] = n;
+    plan[2] = T;
+    std::copy(off.begin(), off.end(), reinterpret_cast<int64_t*>(plan + 4));
+    run(true);
+  }
+  *plan_words = total;
+  return FEA_OK;
+}
+
 // CSR pattern of sum_K (dofs_K x dofs_K): sorted unique columns per row.
 int csr_pattern_impl(int64_t E, int n, const int32_t* dofs, int64_t nrows, int upper, int64_t* row_ptr,
                      int32_t* col_idx, int64_t* nnz) {
@@ -273,4 +380,9 @@ extern "C" int fea_csr_scatter_map(int64_t E, int n, const int32_t* dofs, int64_
 extern "C" int fea_scatter_add_csr_mapped(int64_t E, int n, const void* map, int map_i64, const void* elem,
                                           int elem_f32, int64_t nnz, double* values, void* stream) {
   return fea::scatter_mapped_impl(E, n, map, map_i64, elem, elem_f32, nnz, values, stream);
+}
+
+extern "C" int fea_csr_combine_plan(int64_t E, int n, const void* map, int map_i64, int64_t nnz, int32_t* plan,
+                                    int64_t* plan_words) {
+  return fea::csr_combine_plan_impl(E, n, map, map_i64, nnz, plan, plan_words);
 }

@@ -1,6 +1,7 @@
 // Registry of compiled tile kernels (host side).
 #pragma once
 #include <cstddef>
+#include <cstdint>
 
 #include "layout.h"
 
@@ -42,5 +43,19 @@ const KernelInfo* find_vec_kernel(int form, int p, int prec);
 // The fused local + global assembly form of the streaming kernel `plain`
 // (mass and Helmholtz P1-P3), with an int32 or int64 position map; nullptr if none.
 const void* find_scatter_kernel(const void* plain, int map_i64);
+// Combined global assembly target (pre_combine.cuh): the plan built by
+// fea_csr_combine_plan (32-bit words; header magic kCombineMagic) and the CSR values.
+constexpr int32_t kCombineMagic = 0x46435031;  // "FCP1"
+struct CombineArgs {
+  const int32_t* plan;
+  int64_t plan_words;
+  int64_t nnz;
+  double* values;
+};
+// Elements per tile of the combining plan for local dimension n (min(256, 12800 / n^2), even).
+int combine_tile(int n);
+// The one-pass kernel with tile-combined atomics for (form, degree), and its
+// shared memory at the combining tile; nullptr if none.
+const void* find_combine_kernel(int form, int p, size_t* smem);
 
 }  // namespace fea

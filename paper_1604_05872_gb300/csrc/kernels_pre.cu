@@ -1,6 +1,9 @@
 // Instantiations of the pre-evaluated variant (mass, Helmholtz, elasticity; P1-P4; FP32 and FP64).
+#include <algorithm>
+
 #include "launch.cuh"
 #include "pre.cuh"
+#include "pre_combine.cuh"
 #include "pre_stream.cuh"
 #include "pre_vec.cuh"
 #include "pre_vec_stream.cuh"
@@ -55,6 +58,29 @@ const ScatterKernel kScatterKernels[] = {SCAT(0, 1), SCAT(0, 2), SCAT(0, 3), SCA
 const void* find_scatter_kernel(const void* plain, int map_i64) {
   for (const ScatterKernel& k : kScatterKernels)
     if (k.plain == plain) return map_i64 ? k.map64 : k.map32;
+  return nullptr;
+}
+
+// One-pass assembly with the entries of a tile combined per CSR position.
+int combine_tile(int n) { return std::min(256, std::max(2, (12800 / (n * n)) & ~1)); }
+
+struct CombineKernel {
+  int form, p;
+  const void* fn;
+  size_t (*smem)(int TE);
+};
+template <int F, int P>
+size_t combine_smem(int TE) { return PreCombine<F, P>::smem(TE); }
+#define COMB(F, P) CombineKernel{F, P, reinterpret_cast<const void*>(&pre_combine_kernel<F, P>), &combine_smem<F, P>}
+const CombineKernel kCombineKernels[] = {COMB(0, 1), COMB(0, 2), COMB(0, 3), COMB(1, 1), COMB(1, 2), COMB(1, 3)};
+#undef COMB
+
+const void* find_combine_kernel(int form, int p, size_t* smem) {
+  for (const CombineKernel& k : kCombineKernels)
+    if (k.form == form && k.p == p) {
+      *smem = k.smem(combine_tile(nbasis_c(p)));
+      return k.fn;
+    }
   return nullptr;
 }
 

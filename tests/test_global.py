@@ -252,3 +252,229 @@ def test_gpu_symmetric_storage(fea, orc, form, p):
     # against the oracle's element matrices
     _, _, ref = global_ref.assemble_csr(dofs, orc.assemble(form, p, coords, coeffs), nd, upper=True)
     assert np.linalg.norm(one.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+# ---- combining plan (host builder, checked on the CPU) and the combined one-pass kernel ----
+
+def host_scatter_map(dofs, row_ptr, col_idx, upper=False):
+    """Positions of every (e, i, j) in the CSR values, by a per-entry search (numpy); -2 below
+    the diagonal under symmetric storage."""
+    E, n = dofs.shape
+    m = np.empty((E, n, n), dtype=np.int64)
+    for e in range(E):
+        for i in range(n):
+            r = dofs[e, i]
+            seg = col_idx[row_ptr[r]:row_ptr[r + 1]]
+            for j in range(n):
+                c = dofs[e, j]
+                m[e, i, j] = -2 if (upper and c < r) else row_ptr[r] + int(np.searchsorted(seg, c))
+    return m
+
+
+def decode_combine_plan(plan, E, n):
+    """Tiles of the plan as lists of (position, [tile entries]) in stored order, after checking
+    the layout rules the kernel relies on."""
+    T = min(256, max(2, (12800 // (n * n)) & ~1))
+    assert plan[0] == 0x46435031 and plan[1] == n and plan[2] == T
+    ntiles = (E + T - 1) // T
+    off = plan[4:4 + 2 * (ntiles + 1)].view(np.int64)
+    assert off[0] >= 4 + 2 * (ntiles + 1) and off[-1] == plan.shape[0]
+    tiles = []
+    for t in range(ntiles):
+        a, b = int(off[t]), int(off[t + 1])
+        assert a % 4 == 0 and a < b
+        U, R, L = (int(x) for x in plan[a:a + 3])
+        cw, pw, iw = (R + 3) & ~3, (U + 3) & ~3, ((L + 1) // 2 + 3) & ~3
+        assert a + 4 + cw + pw + iw == b
+        cnt = plan[a + 4:a + 4 + R]
+        assert (R == 0 and U == 0) or (cnt[0] == U and np.all(np.diff(cnt) <= 0) and cnt[-1] > 0)
+        assert int(cnt.sum()) == L
+        pos = plan[a + 4 + cw:a + 4 + cw + U]
+        idx = plan[a + 4 + cw + pw:b].view(np.uint16)[:L]
+        groups = [[] for _ in range(U)]
+        o = 0
+        for r in range(R):
+            for s in range(int(cnt[r])):
+                groups[s].append(int(idx[o + s]))
+            o += int(cnt[r])
+        tiles.append(list(zip(pos.tolist(), groups)))
+    return T, tiles
+
+
+@pytest.mark.parametrize("p,upper,ragged", [(1, False, False), (2, False, True), (2, True, False), (3, False, True)])
+def test_combine_plan_groups_every_entry_at_its_position(p, upper, ragged):
+    """Every stored entry of a tile appears exactly once, under the position the map gives it;
+    positions are distinct within a tile and ordered by their number of entries; entries below
+    the diagonal (symmetric storage) are left out."""
+    import paper_1604_05872_gb300 as fea
+    rng = np.random.default_rng(5 + p)
+    if p < 3:
+        coords, dofs, nd = inputs.box_mesh(3 if p == 2 else 5, p, jitter=0.1)
+        if ragged:
+            dofs = dofs[:-7]
+    else:
+        nd = 400
+        dofs = random_dof_map(75, 20, nd, rng)
+    E, n = dofs.shape
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd, upper=upper)
+    m = host_scatter_map(dofs, row_ptr, col_idx, upper=upper)
+    for dt in (np.int32, np.int64):
+        plan = fea.csr_combine_plan(m.astype(dt), col_idx.shape[0])
+        T, tiles = decode_combine_plan(plan, E, n)
+        nn = n * n
+        for t, slots in enumerate(tiles):
+            flat = m[t * T:(t + 1) * T].reshape(-1)
+            seen = np.zeros(flat.shape[0], dtype=np.int64)
+            for pos, ks in slots:
+                for k in ks:
+                    assert flat[k] == pos
+                    seen[k] += 1
+            assert np.array_equal(seen, (flat != -2).astype(np.int64))
+            assert len({pos for pos, _ in slots}) == len(slots)
+            mult = [len(ks) for _, ks in slots]
+            assert mult == sorted(mult, reverse=True)
+            assert all(k < nn * min(T, E - t * T) for _, ks in slots for k in ks)
+
+
+@pytest.mark.parametrize("form,p", [(0, 1), (1, 2)])
+def test_combined_sums_give_the_reference_global_matrix(orc, form, p):
+    """Summing the oracle's element matrices tile by tile as the plan groups them, one addition
+    per distinct position, reproduces the reference global matrix (a library sparse sum)."""
+    import paper_1604_05872_gb300 as fea
+    rng = np.random.default_rng(23)
+    coords, dofs, nd = inputs.box_mesh(3, p, jitter=0.1)
+    E, n = dofs.shape
+    coeffs = None if form == 0 else inputs.random_coeffs(form, p, E, rng)
+    elem = orc.assemble(form, p, coords, coeffs)
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd)
+    plan = fea.csr_combine_plan(host_scatter_map(dofs, row_ptr, col_idx), col_idx.shape[0])
+    T, tiles = decode_combine_plan(plan, E, n)
+    vals = np.zeros(col_idx.shape[0])
+    adds = 0
+    for t, slots in enumerate(tiles):
+        flat = elem[t * T:(t + 1) * T].reshape(-1)
+        for pos, ks in slots:
+            vals[pos] += flat[ks].sum()
+            adds += 1
+    _, _, ref = global_ref.assemble_csr(dofs, elem, nd)
+    assert np.abs(vals - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert adds < E * n * n  # entries of a tile that meet were combined
+
+
+def test_combine_plan_rejects_bad_maps():
+    import ctypes
+    import paper_1604_05872_gb300 as fea
+    _, dofs, nd = inputs.box_mesh(2, 1)
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd)
+    m = host_scatter_map(dofs, row_ptr, col_idx)
+    nnz = col_idx.shape[0]
+    for bad_value in (nnz, -1, -3):
+        bad = m.copy()
+        bad[3, 1, 2] = bad_value
+        with pytest.raises(fea.FeaError) as e:
+            fea.csr_combine_plan(bad, nnz)
+        assert e.value.code == fea.EINVAL
+    with pytest.raises(fea.FeaError):  # 32-bit positions only
+        fea.csr_combine_plan(m, 2 ** 31)
+    with pytest.raises(fea.FeaError):  # 16-bit tile entries: n^2 T <= 65536
+        fea.csr_combine_plan(np.zeros((1, 182, 182), dtype=np.int32), 1)
+    # a buffer smaller than the size query is refused
+    words = ctypes.c_int64(0)
+    lib = fea.load()
+    mm = np.ascontiguousarray(m)
+    assert lib.fea_csr_combine_plan(mm.shape[0], 4, mm.ctypes.data, 1, nnz, None, ctypes.byref(words)) == 0
+    buf = np.zeros(words.value, dtype=np.int32)
+    small = ctypes.c_int64(words.value - 1)
+    assert lib.fea_csr_combine_plan(mm.shape[0], 4, mm.ctypes.data, 1, nnz, buf.ctypes.data,
+                                    ctypes.byref(small)) == fea.EINVAL
+    # an empty mesh: a header and one offset
+    plan = fea.csr_combine_plan(np.zeros((0, 4, 4), dtype=np.int32), 0)
+    assert plan.shape[0] == 8 and plan[0] == 0x46435031
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form,p,mesh", [(0, 1, True), (1, 1, True), (1, 2, True), (0, 2, True),
+                                         (1, 3, False), (0, 3, False)])
+@pytest.mark.parametrize("upper", [False, True])
+def test_gpu_combined_global_assembly(fea, orc, form, p, mesh, upper):
+    """fea_assemble_csr_combined against the two-pass assembly on the same inputs (the order of the
+    FP64 additions only) and against the reference global matrix of the oracle's element
+    matrices (the FP32 contraction's tolerance); full and symmetric storage; ragged last tile."""
+    import torch
+    rng = np.random.default_rng(41 + p)
+    if mesh:
+        coords, dofs, nd = inputs.box_mesh(6, p, jitter=0.1)  # 1296 elements, a ragged last tile
+    else:
+        E, n = 1111, fea.local_dim(form, p)
+        coords, _ = inputs.workload(form, p, E, seed=inputs.SEED + 37)
+        nd = 3000
+        dofs = random_dof_map(E, n, nd, rng)
+    E = coords.shape[0]
+    coeffs = None if form == 0 else inputs.random_coeffs(form, p, E, rng)
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd, upper=upper)
+    c = torch.from_numpy(coords).cuda()
+    f = None if coeffs is None else torch.from_numpy(inputs.coeff_array(form, p, coeffs)).cuda()
+    dd, rp, ci = (torch.from_numpy(x).cuda() for x in (dofs, row_ptr, col_idx))
+    smap = fea.csr_scatter_map(dd, rp, ci, upper=upper)
+    plan = torch.from_numpy(fea.csr_combine_plan(smap, col_idx.shape[0])).cuda()
+    vals = fea.assemble_csr_combined(form, p, c, f, plan,
+                                     torch.zeros(col_idx.shape[0], dtype=torch.float64, device="cuda"))
+    two = fea.scatter_add_csr_mapped(smap, fea.assemble(form, p, c, f), torch.zeros_like(vals))
+    fea.sync()
+    assert torch.allclose(vals, two, rtol=0, atol=1e-12 * float(two.abs().max()))
+    _, _, ref = global_ref.assemble_csr(dofs, orc.assemble(form, p, coords, coeffs), nd, upper=upper)
+    got = vals.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    fea.assemble_csr_combined(form, p, c, f, plan, vals)  # accumulates
+    fea.sync()
+    assert torch.allclose(vals, 2 * two, rtol=0, atol=1e-12 * float(two.abs().max()))
+
+
+@pytest.mark.gpu
+def test_gpu_combined_rejects_and_flags(fea):
+    """Wrong form or degree, a short or misaligned plan: refused on the host.  A plan of another
+    tile size or with a position outside the values: flagged (FEA_EINVAL at the next sync), the
+    offending tile or position skipped, every other position added."""
+    import torch
+    coords, dofs, nd = inputs.box_mesh(3, 1)  # 162 elements: one tile of 256 at P1
+    c = torch.from_numpy(coords).cuda()
+    row_ptr, col_idx = fea.csr_pattern(dofs, nd)
+    nnz = col_idx.shape[0]
+    smap = fea.csr_scatter_map(torch.from_numpy(dofs).cuda(), torch.from_numpy(row_ptr).cuda(),
+                               torch.from_numpy(col_idx).cuda())
+    host = fea.csr_combine_plan(smap, nnz)
+    plan = torch.from_numpy(host).cuda()
+    vals = torch.zeros(nnz, dtype=torch.float64, device="cuda")
+    fea.sync()
+    with pytest.raises(fea.FeaError) as e:  # no combined kernel for the vector forms
+        fea.assemble_csr_combined(2, 1, c, torch.zeros(c.shape[0] * 8, dtype=torch.float64, device="cuda"), plan, vals)
+    assert e.value.code == fea.EINVAL
+    with pytest.raises(fea.FeaError):  # nor for P4
+        fea.assemble_csr_combined(0, 4, c, None, plan, vals)
+    with pytest.raises(fea.FeaError):  # shorter than its header for this many elements
+        fea.assemble_csr_combined(0, 1, c, None, plan[:5], vals)
+    with pytest.raises(fea.FeaError):  # not 16-byte aligned
+        fea.assemble_csr_combined(0, 1, c, None, plan[1:], vals)
+    # a plan for the P2 tile size used at P1: the kernel refuses it whole
+    other = host.copy()
+    other[2] = 128
+    fea.assemble_csr_combined(0, 1, c, None, torch.from_numpy(other).cuda(), vals)
+    with pytest.raises(fea.FeaError) as e:
+        fea.sync()
+    assert e.value.code == fea.EINVAL
+    assert float(vals.abs().sum()) == 0.0
+    # one position outside the values: that position is skipped, the rest added
+    a = int(host[4:6].view(np.int64)[0])
+    R, U = int(host[a + 1]), int(host[a])
+    pos_at = a + 4 + ((R + 3) & ~3)
+    bad = host.copy()
+    bad[pos_at + U - 1] = nnz + 5
+    fea.assemble_csr_combined(0, 1, c, None, torch.from_numpy(bad).cuda(), vals)
+    with pytest.raises(fea.FeaError) as e:
+        fea.sync()
+    assert e.value.code == fea.EINVAL
+    full = fea.assemble_csr_combined(0, 1, c, None, plan, torch.zeros_like(vals))
+    fea.sync()
+    skipped = int(host[pos_at + U - 1])
+    diff = (full - vals).cpu().numpy()
+    assert diff[skipped] == float(full[skipped]) and np.delete(diff, skipped).max() == 0.0
