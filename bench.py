@@ -662,14 +662,16 @@ def run_bernstein(args, fea, torch, barrier, max_over_ranks, world, rank, local)
 
 def run_global(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     """Local and global assembly together (the paper times them jointly): Helmholtz P2 on a
-    conforming mesh of the unit cube (55^3 cubes x 6 tetrahedra = 998 250 elements, 1.37 M DOFs).
+    conforming mesh of the unit cube (55^3 cubes x 6 tetrahedra = 998 250 elements, 1.37 M DOFs;
+    --elements picks the nearest cube mesh for profiling).
     One step: zero the CSR values, then fea_assemble_csr_combined (element matrices summed per
     distinct CSR position of a tile in shared memory, one FP64 atomic per position, never
     stored; the positions and their grouping computed once per mesh).  Also timed: the one-pass
     kernel with one atomic per entry (fea_assemble_csr), the two-pass form (fea_assemble, then
     fea_scatter_add_csr_mapped), the scatters alone and symmetric storage."""
     from paper_1604_05872_gb300 import inputs
-    coords, dofs, nd = inputs.box_mesh(55, 2, jitter=0.1, seed=inputs.SEED + rank)
+    m = 55 if not args.elements else max(2, int(round((args.elements / 6) ** (1 / 3))))  # cubes per edge
+    coords, dofs, nd = inputs.box_mesh(m, 2, jitter=0.1, seed=inputs.SEED + rank)
     E = coords.shape[0]
     rng = np.random.Generator(np.random.PCG64(inputs.SEED + 7 + rank))
     f = inputs.random_coeffs(1, 2, E, rng)

@@ -27,11 +27,14 @@
 //                       holding the r-th entry of positions 0 .. cnt[r] - 1;
 //                       each of the three arrays padded to a multiple of 4 words.
 //
-// Thread s of the combine phase sums the entries of positions s, s + NT, ...
-// round by round, so consecutive threads read consecutive words of pos and idx.
-// Every plan read stays inside the tile record, every stage read inside the
-// tile's entries and every atomic inside [0, nnz): a plan that breaks a bound is
-// flagged (ERR_PATTERN) and the offending entry or tile skipped.
+// Each tile's record reaches shared memory by one bulk copy (the TMA engine),
+// issued when the tile starts and overlapping its contraction; thread s of the
+// combine phase then sums the entries of positions s, s + NT, ... round by round
+// from shared memory alone.  Tiles hold at most 6400 entries (T = min(128,
+// 6400 / n^2)), so a record never exceeds PW words.  Every plan read stays
+// inside the tile record, every stage read inside the tile's entries and every
+// atomic inside [0, nnz): a plan that breaks a bound is flagged (ERR_PATTERN) and
+// the offending entry or tile skipped.
 #pragma once
 #include "common.cuh"
 #include "kernels.h"
@@ -55,8 +58,11 @@ __device__ __forceinline__ double f2d_exact(float f) {
 template <int FORM, int P>
 struct PreCombine {
   using K = PreStream<FORM, P>;
+  static constexpr int TC = (6400 / K::NN) < 2 ? 2 : (6400 / K::NN > 128 ? 128 : (6400 / K::NN) & ~1);  // tile
+  static constexpr int PW = 4 + round_up(TC, 4) + round_up(TC * K::NN, 4) + round_up((TC * K::NN + 1) / 2, 4);
   FEA_HD static size_t off_stage(int TE) { return K::off_bar(TE) + 32; }
-  FEA_HD static size_t smem(int TE) { return off_stage(TE) + round_up_sz((size_t)TE * K::NN * 4, 16); }
+  FEA_HD static size_t off_plan(int TE) { return off_stage(TE) + round_up_sz((size_t)TE * K::NN * 4, 16); }
+  FEA_HD static size_t smem(int TE) { return off_plan(TE) + (size_t)PW * 4; }
 };
 
 template <int FORM, int P>
@@ -69,7 +75,9 @@ __global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, 
   float* H = reinterpret_cast<float*>(sm + K::off_h(TE));  // [2][TE][NHP]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + K::off_bar(TE));
   float* stage = reinterpret_cast<float*>(sm + C::off_stage(TE));  // [TE][NN]
-  __shared__ int s_abort;
+  int32_t* rec = reinterpret_cast<int32_t*>(sm + C::off_plan(TE));  // [PW]: the tile's plan record
+  __shared__ __align__(8) uint64_t rec_bar;
+  __shared__ int s_abort, s_rec_words;
   const TabLayout L = tab_layout(q.Q, K::NS, K::RTAB);
   const float* Rg = reinterpret_cast<const float*>(q.tab) + L.offR;
   const int64_t ntiles = (q.E + TE - 1) / TE;
@@ -86,7 +94,7 @@ __global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, 
   // the plan must be for this local dimension and tile (the host checked its size)
   const int64_t hdr = 4 + 2 * (ntiles + 1);
   if (cb.plan_words < hdr || __ldg(cb.plan) != kCombineMagic || __ldg(cb.plan + 1) != K::NS ||
-      __ldg(cb.plan + 2) != TE) {
+      __ldg(cb.plan + 2) != TE || TE != C::TC) {
     if (threadIdx.x == 0) flag_error(err, ERR_PATTERN);
     return;
   }
@@ -121,39 +129,55 @@ __global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, 
   auto abort_all = [&](int j_lo, int j_hi) {
     for (int j = j_lo; j <= j_hi && j < my_tiles; ++j) wait_in(j);
   };
+  // thread 0: bulk copy of the plan record of tile j (offsets a, b) into rec, or
+  // a bare arrival when the record breaks a bound (s_rec_words = -1)
+  auto issue_rec = [&](int64_t a, int64_t b) {
+    const bool ok = a >= hdr && !(a & 3) && b <= cb.plan_words && a + 4 <= b && b - a <= C::PW;
+    s_rec_words = ok ? (int)(b - a) : -1;
+    fence_proxy_async();
+    mbar_expect_tx(&rec_bar, ok ? (unsigned)(b - a) * 4u : 0u);
+    if (ok) bulk_g2s(rec, cb.plan + a, (unsigned)(b - a) * 4u, &rec_bar);
+  };
   // one FP64 atomic per distinct position of tile j, its entries summed from the stage
   auto combine = [&](int j) {
-    const int64_t tile = first + (int64_t)j * stride;
     const int lim = tile_ne(j) * K::NN;
-    const int64_t a = __ldg(toff + tile), b = __ldg(toff + tile + 1);
-    if (a < hdr || (a & 3) || b > cb.plan_words || a + 4 > b) {
+    const int words = s_rec_words;
+    if (words < 0) {
       if (t == 0) flag_error(err, ERR_PATTERN);
       return;
     }
-    const int4 h = __ldg(reinterpret_cast<const int4*>(cb.plan + a));
-    const int U = h.x, R = h.y, Ln = h.z;
-    const int64_t cw = ((int64_t)R + 3) & ~3ll, pw = ((int64_t)U + 3) & ~3ll, iw = (((int64_t)Ln + 1) / 2 + 3) & ~3ll;
-    if (U < 0 || R < 0 || Ln < U || Ln > lim || a + 4 + cw + pw + iw > b) {
+    const int U = rec[0], R = rec[1], Ln = rec[2];
+    if (U < 0 || R < 0 || R > TE || Ln < U || Ln > lim || (U > 0) != (R > 0)) {
       if (t == 0) flag_error(err, ERR_PATTERN);
       return;
     }
-    const int32_t* cnt = cb.plan + a + 4;
+    const int cw = (R + 3) & ~3, pw = (U + 3) & ~3, iw = ((Ln + 1) / 2 + 3) & ~3;
+    if (4 + cw + pw + iw > words || (R > 0 && rec[4] != U)) {
+      if (t == 0) flag_error(err, ERR_PATTERN);
+      return;
+    }
+    const int32_t* cnt = rec + 4;
     const int32_t* pos = cnt + cw;
     const uint16_t* idx = reinterpret_cast<const uint16_t*>(pos + pw);
-    for (int s = t; s < U; s += NT) {
-      double acc = 0.0;
-      int64_t off = 0;
-      bool bad = false;
-      for (int r = 0; r < R; ++r) {
-        const int c = __ldg(cnt + r);
+    for (int s = t; s < U; s += NT) {  // round 0: every position has an entry (cnt[0] == U)
+      int k = idx[s];
+      bool bad = k >= lim;
+      double acc = bad ? 0.0 : f2d_exact(stage[k]);
+      int off = U;
+      for (int r = 1; r < R; ++r) {
+        const int c = cnt[r];
         if (s >= c) break;
-        const int64_t o = off + s;
-        const int k = o < Ln ? (int)__ldg(idx + o) : lim;
+        const int o = off + s;
+        if (o >= Ln) {
+          bad = true;
+          break;
+        }
+        k = idx[o];
         if (k < lim) acc += f2d_exact(stage[k]);
         else bad = true;
         off += c;
       }
-      const int64_t m = __ldg(pos + s);
+      const int64_t m = pos[s];
       if (m >= 0 && m < cb.nnz) atomicAdd(cb.values + m, acc);
       else bad = true;
       if (bad) flag_error(err, ERR_PATTERN);
@@ -163,6 +187,7 @@ __global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, 
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&rec_bar, 1);
     fence_barrier_init();
     s_abort = 0;
   }
@@ -183,9 +208,22 @@ __global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, 
   geometry(0);
   __syncthreads();
 
+  // record offsets of the next tile, loaded one tile ahead by thread 0
+  int64_t ra = 0, rb = 0;
+  if (t == 0) {
+    ra = __ldg(toff + first);
+    rb = __ldg(toff + first + 1);
+  }
   for (int j = 0; j < my_tiles; ++j) {
     const int ne = tile_ne(j);
-    if (t == 0 && j + 2 < my_tiles) issue(j + 2);
+    if (t == 0) {
+      if (j + 2 < my_tiles) issue(j + 2);
+      issue_rec(ra, rb);  // rec is free: the combine of tile j - 1 ended before the last barrier
+      if (j + 1 < my_tiles) {
+        ra = __ldg(toff + first + (int64_t)(j + 1) * stride);
+        rb = __ldg(toff + first + (int64_t)(j + 1) * stride + 1);
+      }
+    }
     if (active) {
       float r0[K::R], r1[K::R];
 #pragma unroll
@@ -237,7 +275,12 @@ __global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, 
       }
     }
     __syncthreads();  // the stage holds tile j
-    combine(j);
+    if (mbar_wait(&rec_bar, (unsigned)j & 1u)) {
+      combine(j);
+    } else {
+      flag_error(err, ERR_TIMEOUT);
+      s_abort = 1;
+    }
     // inputs of tile j + 1 -> geometry into the other H buffer
     if (j + 1 < my_tiles) {
       if (wait_in(j + 1)) {

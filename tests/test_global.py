@@ -274,7 +274,7 @@ def host_scatter_map(dofs, row_ptr, col_idx, upper=False):
 def decode_combine_plan(plan, E, n):
     """Tiles of the plan as lists of (position, [tile entries]) in stored order, after checking
     the layout rules the kernel relies on."""
-    T = min(256, max(2, (12800 // (n * n)) & ~1))
+    T = min(128, max(2, (6400 // (n * n)) & ~1))
     assert plan[0] == 0x46435031 and plan[1] == n and plan[2] == T
     ntiles = (E + T - 1) // T
     off = plan[4:4 + 2 * (ntiles + 1)].view(np.int64)
@@ -436,7 +436,7 @@ def test_gpu_combined_rejects_and_flags(fea):
     tile size or with a position outside the values: flagged (FEA_EINVAL at the next sync), the
     offending tile or position skipped, every other position added."""
     import torch
-    coords, dofs, nd = inputs.box_mesh(3, 1)  # 162 elements: one tile of 256 at P1
+    coords, dofs, nd = inputs.box_mesh(2, 1)  # 48 elements: one tile of 128 at P1
     c = torch.from_numpy(coords).cuda()
     row_ptr, col_idx = fea.csr_pattern(dofs, nd)
     nnz = col_idx.shape[0]
@@ -457,7 +457,7 @@ def test_gpu_combined_rejects_and_flags(fea):
         fea.assemble_csr_combined(0, 1, c, None, plan[1:], vals)
     # a plan for the P2 tile size used at P1: the kernel refuses it whole
     other = host.copy()
-    other[2] = 128
+    other[2] = 64
     fea.assemble_csr_combined(0, 1, c, None, torch.from_numpy(other).cuda(), vals)
     with pytest.raises(fea.FeaError) as e:
         fea.sync()
