@@ -249,7 +249,7 @@ int fea_assemble_csr(int form, int degree, int64_t E, const double* coords, cons
 /* Combining plan of the one-pass global assembly (HOST arrays, no GPU needed),
  * computed once per mesh from the position map of fea_csr_scatter_map (copied
  * to the host; [E][n][n], int32 when map_i64 = 0, else int64): for every tile of
- * T = min(128, 6400 / n^2 rounded down to even) consecutive elements, the
+ * T = min(128, 3200 / n^2 rounded down to even) consecutive elements, the
  * distinct CSR positions the tile's entries fall on and, per position, which of
  * the tile's entries add to it (Section 2: the global matrix is the sum of the
  * element matrices at their global DOFs; entries of one tile meeting at one

@@ -52,7 +52,7 @@ struct CombineArgs {
   int64_t nnz;
   double* values;
 };
-// Elements per tile of the combining plan for local dimension n (min(128, 6400 / n^2), even).
+// Elements per tile of the combining plan for local dimension n (min(128, 3200 / n^2), even).
 int combine_tile(int n);
 // The one-pass kernel with tile-combined atomics for (form, degree), and its
 // shared memory at the combining tile; nullptr if none.

@@ -62,7 +62,7 @@ const void* find_scatter_kernel(const void* plain, int map_i64) {
 }
 
 // One-pass assembly with the entries of a tile combined per CSR position.
-int combine_tile(int n) { return std::min(128, std::max(2, (6400 / (n * n)) & ~1)); }
+int combine_tile(int n) { return std::min(128, std::max(2, (3200 / (n * n)) & ~1)); }
 
 struct CombineKernel {
   int form, p;

@@ -9,8 +9,8 @@
 // (FP32), then every distinct CSR position the tile touches is summed from the
 // stage in FP64 (each entry widened exactly, so the result differs from the
 // two-pass assembly only in the order of the FP64 additions) and added to the
-// CSR values with one FP64 atomic.  On the cube mesh at P2, 56% of a tile's
-// entries fall on distinct positions: 56 atomics per element instead of 100.
+// CSR values with one FP64 atomic.  On the cube mesh at P2, 57% of a tile's
+// entries fall on distinct positions: 57 atomics per element instead of 100.
 //
 // Which entries meet at which position depends on the mesh alone; the host
 // computes it once per mesh, per tile of T elements (fea_csr_combine_plan), as a
@@ -30,8 +30,10 @@
 // Each tile's record reaches shared memory by one bulk copy (the TMA engine),
 // issued when the tile starts and overlapping its contraction; thread s of the
 // combine phase then sums the entries of positions s, s + NT, ... round by round
-// from shared memory alone.  Tiles hold at most 6400 entries (T = min(128,
-// 6400 / n^2)), so a record never exceeds PW words.  Every plan read stays
+// from shared memory alone, two positions per thread in flight.  Tiles hold at
+// most 3200 entries (T = min(128, 3200 / n^2): 32 elements at P2, so that with
+// 64 registers four CTAs fit on an SM; the combine phase is latency-bound and
+// lives on resident warps), so a record never exceeds PW words.  Every plan read stays
 // inside the tile record, every stage read inside the tile's entries and every
 // atomic inside [0, nnz): a plan that breaks a bound is flagged (ERR_PATTERN) and
 // the offending entry or tile skipped.
@@ -58,7 +60,7 @@ __device__ __forceinline__ double f2d_exact(float f) {
 template <int FORM, int P>
 struct PreCombine {
   using K = PreStream<FORM, P>;
-  static constexpr int TC = (6400 / K::NN) < 2 ? 2 : (6400 / K::NN > 128 ? 128 : (6400 / K::NN) & ~1);  // tile
+  static constexpr int TC = (3200 / K::NN) < 2 ? 2 : (3200 / K::NN > 128 ? 128 : (3200 / K::NN) & ~1);  // tile
   static constexpr int PW = 4 + round_up(TC, 4) + round_up(TC * K::NN, 4) + round_up((TC * K::NN + 1) / 2, 4);
   FEA_HD static size_t off_stage(int TE) { return K::off_bar(TE) + 32; }
   FEA_HD static size_t off_plan(int TE) { return off_stage(TE) + round_up_sz((size_t)TE * K::NN * 4, 16); }
@@ -66,7 +68,7 @@ struct PreCombine {
 };
 
 template <int FORM, int P>
-__global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, unsigned* err) {
+__global__ void __launch_bounds__(NT, P == 2 ? 4 : 1) pre_combine_kernel(Req q, CombineArgs cb, unsigned* err) {
   using K = PreStream<FORM, P>;
   using C = PreCombine<FORM, P>;
   extern __shared__ __align__(16) char sm[];
@@ -159,27 +161,44 @@ __global__ void __launch_bounds__(NT) pre_combine_kernel(Req q, CombineArgs cb, 
     const int32_t* cnt = rec + 4;
     const int32_t* pos = cnt + cw;
     const uint16_t* idx = reinterpret_cast<const uint16_t*>(pos + pw);
-    for (int s = t; s < U; s += NT) {  // round 0: every position has an entry (cnt[0] == U)
-      int k = idx[s];
-      bool bad = k >= lim;
-      double acc = bad ? 0.0 : f2d_exact(stage[k]);
+    constexpr int IL = 2;  // positions per thread in flight (independent FP64 chains)
+    for (int s0 = t; s0 < U; s0 += IL * NT) {
+      int kk[IL];
+      double acc[IL];
+      bool bad = false;
+#pragma unroll
+      for (int i = 0; i < IL; ++i) {
+        const int s = s0 + i * NT;
+        kk[i] = s < U ? idx[s] : 0;
+        bad |= kk[i] >= lim;
+        acc[i] = (s < U && kk[i] < lim) ? f2d_exact(stage[kk[i]]) : 0.0;
+      }
       int off = U;
       for (int r = 1; r < R; ++r) {
         const int c = cnt[r];
-        if (s >= c) break;
-        const int o = off + s;
-        if (o >= Ln) {
-          bad = true;
-          break;
+        if (s0 >= c) break;
+#pragma unroll
+        for (int i = 0; i < IL; ++i) {
+          const int s = s0 + i * NT, o = off + s;
+          const bool on = s < c && o < Ln;
+          if (s < c && o >= Ln) bad = true;
+          kk[i] = on ? idx[o] : 0;
+          if (on) {
+            if (kk[i] < lim) acc[i] += f2d_exact(stage[kk[i]]);
+            else bad = true;
+          }
         }
-        k = idx[o];
-        if (k < lim) acc += f2d_exact(stage[k]);
-        else bad = true;
         off += c;
       }
-      const int64_t m = pos[s];
-      if (m >= 0 && m < cb.nnz) atomicAdd(cb.values + m, acc);
-      else bad = true;
+#pragma unroll
+      for (int i = 0; i < IL; ++i) {
+        const int s = s0 + i * NT;
+        if (s < U) {
+          const int64_t m = pos[s];
+          if (m >= 0 && m < cb.nnz) atomicAdd(cb.values + m, acc[i]);
+          else bad = true;
+        }
+      }
       if (bad) flag_error(err, ERR_PATTERN);
     }
   };

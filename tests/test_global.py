@@ -274,7 +274,7 @@ def host_scatter_map(dofs, row_ptr, col_idx, upper=False):
 def decode_combine_plan(plan, E, n):
     """Tiles of the plan as lists of (position, [tile entries]) in stored order, after checking
     the layout rules the kernel relies on."""
-    T = min(128, max(2, (6400 // (n * n)) & ~1))
+    T = min(128, max(2, (3200 // (n * n)) & ~1))
     assert plan[0] == 0x46435031 and plan[1] == n and plan[2] == T
     ntiles = (E + T - 1) // T
     off = plan[4:4 + 2 * (ntiles + 1)].view(np.int64)
