@@ -122,7 +122,7 @@ def test_global_assembly_full_size(fea, orc):
     assembled load vector (the stiffness rows sum to zero, the f-mass rows to int f phi_i), checked
     against the oracle's element load vectors summed at the global DOFs, to the FP32 contraction's
     tolerance relative to each row's absolute sum; symmetric storage holds the upper triangle of the
-    full matrix."""
+    full matrix; the combining kernel gives both up to the order of the FP64 additions."""
     import torch
     coords, dofs, nd = inputs.box_mesh(55, 2, jitter=0.1, seed=inputs.SEED)
     E = coords.shape[0]
@@ -149,3 +149,12 @@ def test_global_assembly_full_size(fea, orc):
     r = np.repeat(np.arange(nd), np.diff(row_ptr))
     keep = col_idx >= r
     assert np.allclose(uv.cpu().numpy(), v[keep], rtol=0, atol=1e-12 * np.abs(v).max())
+    # the combining kernel that bench.py times (a tile's entries summed per CSR position): the same
+    # matrix up to the order of the FP64 additions, full and symmetric storage
+    plan = torch.from_numpy(fea.csr_combine_plan(smap, col_idx.shape[0])).cuda()
+    cv = fea.assemble_csr_combined(1, 2, c, fc, plan, torch.zeros_like(vals))
+    uplan = torch.from_numpy(fea.csr_combine_plan(umap, uc.shape[0])).cuda()
+    cu = fea.assemble_csr_combined(1, 2, c, fc, uplan, torch.zeros_like(uv))
+    fea.sync()
+    assert np.allclose(cv.cpu().numpy(), v, rtol=0, atol=1e-12 * np.abs(v).max())
+    assert np.allclose(cu.cpu().numpy(), uv.cpu().numpy(), rtol=0, atol=1e-12 * np.abs(v).max())
