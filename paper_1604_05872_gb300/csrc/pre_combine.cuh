@@ -28,9 +28,11 @@
 //                       each of the three arrays padded to a multiple of 4 words.
 //
 // Each tile's record reaches shared memory by one bulk copy (the TMA engine),
-// issued when the tile starts and overlapping its contraction; thread s of the
-// combine phase then sums the entries of positions s, s + NT, ... round by round
-// from shared memory alone, two positions per thread in flight.  Tiles hold at
+// issued when the tile starts and overlapping its contraction.  After the
+// contraction the first warps (one lane per element) form the next tile's FP64
+// geometry while the other threads combine: combining thread s sums the entries
+// of positions s, s + NCT, ... round by round from shared memory alone, two
+// positions per thread in flight.  Tiles hold at
 // most 3200 entries (T = min(128, 3200 / n^2): 32 elements at P2, so that with
 // 64 registers four CTAs fit on an SM; the combine phase is latency-bound and
 // lives on resident warps), so a record never exceeds PW words.  Every plan read stays
@@ -107,6 +109,10 @@ __global__ void __launch_bounds__(NT, P == 2 ? 4 : 1) pre_combine_kernel(Req q, 
   const int t = threadIdx.x;
   const bool active = t < K::G * K::S;
   const int slot = t % K::S, g0 = t / K::S;
+  // after the contraction the first GWT threads (whole warps, one lane per element)
+  // form the next tile's geometry while the other NCT threads combine this tile
+  constexpr int GWT = (C::TC + 31) / 32 * 32, NCT = NT - GWT;
+  static_assert(NCT >= 64, "combining threads");
 
   auto tile_ne = [&](int j) {
     const int64_t e0 = (first + (int64_t)j * stride) * TE;
@@ -142,33 +148,34 @@ __global__ void __launch_bounds__(NT, P == 2 ? 4 : 1) pre_combine_kernel(Req q, 
   };
   // one FP64 atomic per distinct position of tile j, its entries summed from the stage
   auto combine = [&](int j) {
+    const int tc = t - GWT;  // this thread's rank among the combining threads
     const int lim = tile_ne(j) * K::NN;
     const int words = s_rec_words;
     if (words < 0) {
-      if (t == 0) flag_error(err, ERR_PATTERN);
+      if (tc == 0) flag_error(err, ERR_PATTERN);
       return;
     }
     const int U = rec[0], R = rec[1], Ln = rec[2];
     if (U < 0 || R < 0 || R > TE || Ln < U || Ln > lim || (U > 0) != (R > 0)) {
-      if (t == 0) flag_error(err, ERR_PATTERN);
+      if (tc == 0) flag_error(err, ERR_PATTERN);
       return;
     }
     const int cw = (R + 3) & ~3, pw = (U + 3) & ~3, iw = ((Ln + 1) / 2 + 3) & ~3;
     if (4 + cw + pw + iw > words || (R > 0 && rec[4] != U)) {
-      if (t == 0) flag_error(err, ERR_PATTERN);
+      if (tc == 0) flag_error(err, ERR_PATTERN);
       return;
     }
     const int32_t* cnt = rec + 4;
     const int32_t* pos = cnt + cw;
     const uint16_t* idx = reinterpret_cast<const uint16_t*>(pos + pw);
     constexpr int IL = 2;  // positions per thread in flight (independent FP64 chains)
-    for (int s0 = t; s0 < U; s0 += IL * NT) {
+    for (int s0 = tc; s0 < U; s0 += IL * NCT) {
       int kk[IL];
       double acc[IL];
       bool bad = false;
 #pragma unroll
       for (int i = 0; i < IL; ++i) {
-        const int s = s0 + i * NT;
+        const int s = s0 + i * NCT;
         kk[i] = s < U ? idx[s] : 0;
         bad |= kk[i] >= lim;
         acc[i] = (s < U && kk[i] < lim) ? f2d_exact(stage[kk[i]]) : 0.0;
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(NT, P == 2 ? 4 : 1) pre_combine_kernel(Req q, 
         if (s0 >= c) break;
 #pragma unroll
         for (int i = 0; i < IL; ++i) {
-          const int s = s0 + i * NT, o = off + s;
+          const int s = s0 + i * NCT, o = off + s;
           const bool on = s < c && o < Ln;
           if (s < c && o >= Ln) bad = true;
           kk[i] = on ? idx[o] : 0;
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(NT, P == 2 ? 4 : 1) pre_combine_kernel(Req q, 
       }
 #pragma unroll
       for (int i = 0; i < IL; ++i) {
-        const int s = s0 + i * NT;
+        const int s = s0 + i * NCT;
         if (s < U) {
           const int64_t m = pos[s];
           if (m >= 0 && m < cb.nnz) atomicAdd(cb.values + m, acc[i]);
@@ -294,20 +301,21 @@ __global__ void __launch_bounds__(NT, P == 2 ? 4 : 1) pre_combine_kernel(Req q, 
       }
     }
     __syncthreads();  // the stage holds tile j
-    if (mbar_wait(&rec_bar, (unsigned)j & 1u)) {
+    if (t < GWT) {
+      // inputs of tile j + 1 -> geometry into the other H buffer
+      if (j + 1 < my_tiles) {
+        if (wait_in(j + 1)) {
+          geometry(j + 1);
+        } else {
+          flag_error(err, ERR_TIMEOUT);
+          s_abort = 1;
+        }
+      }
+    } else if (mbar_wait(&rec_bar, (unsigned)j & 1u)) {
       combine(j);
     } else {
       flag_error(err, ERR_TIMEOUT);
       s_abort = 1;
-    }
-    // inputs of tile j + 1 -> geometry into the other H buffer
-    if (j + 1 < my_tiles) {
-      if (wait_in(j + 1)) {
-        geometry(j + 1);
-      } else {
-        flag_error(err, ERR_TIMEOUT);
-        s_abort = 1;
-      }
     }
     __syncthreads();  // the stage is free, H of tile j + 1 is complete
     if (s_abort) {
