@@ -270,7 +270,8 @@ NEO_POINT_FP64_TC = 3 + 18 + 3 + 13
 def precision_of(args, fea, form, p):
     """(precision code, name, uses the tensor-core kernel) for a (form, degree)."""
     names = {"fp32": fea.PREC_FP32, "bf16x2": fea.PREC_BF16X2, "fp64": fea.PREC_FP64}
-    tc = fea.plan(form, p, precision=fea.PREC_BF16X2)["threads"] != 256
+    f32 = bool(args.out_f32)  # a tensor-core kernel exists where the split-BF16 plan differs from the FP32 one
+    tc = fea.plan(form, p, precision=fea.PREC_BF16X2, out_f32=f32) != fea.plan(form, p, precision=fea.PREC_FP32, out_f32=f32)
     if args.precision == "auto":
         return (fea.PREC_BF16X2, "bf16x2", True) if tc else (fea.PREC_FP32, "fp32", False)
     prec = names[args.precision]
@@ -283,9 +284,14 @@ def tc_flops_per_element(form, p):
     symmetric basis pairs (hi and lo parts), 9 columns (c, d) per element,
     K = 9 (Q + 1) (the points and the point-summed term), two passes (hi and lo
     parts of H).  P3 (one product per element): the 3 n_s x 3 n_s blocks S and T
-    over the Q points, three split chains (hi hi, hi lo, lo hi)."""
+    over the Q points, three split chains (hi hi, hi lo, lo hi).  Mass and Helmholtz
+    (FP32 output): the pre-evaluated contraction, r terms x n_s^2 entries, four split
+    products."""
     ns = (p + 1) * (p + 2) * (p + 3) // 6
     Q = (p + 1) ** 3
+    if form in (0, 1):  # pre-evaluated scalar forms: [elements x r] x [r x n^2], four split products
+        r = 1 if form == 0 else 6 + ns
+        return 2 * 4 * r * ns * ns
     if p == 2:
         return 2 * 2 * (ns * (ns + 1)) * 9 * 9 * (Q + 1)
     return 2 * 3 * 2 * (3 * ns) ** 2 * Q
@@ -377,7 +383,7 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     esz = 4 if f32 else 8
     stream = torch.cuda.current_stream()
     prec, prec_name, tc = precision_of(args, fea, form, p)
-    pl = fea.plan(form, p, precision=prec)
+    pl = fea.plan(form, p, precision=prec, out_f32=f32)
     bytes_elem = 96 + 8 * fea.coeff_len(form, p) + esz * n * n
 
     for _ in range(args.warmup):
@@ -447,7 +453,8 @@ def run_single(args, fea, torch, barrier, max_over_ranks, world, rank, local):
     hbm, peak_kind = peaks()
     alg_bytes = E * bytes_elem
     flops = E * (tc_flops_per_element(form, p) if tc else pl["flops_run"])
-    f64 = E * (30 + NEO_POINT_FP64_TC * pl["quad_points"] if tc else fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]))
+    f64 = E * (30 + NEO_POINT_FP64_TC * pl["quad_points"] if tc and form == 3
+               else fp64_ops_per_element(form, p, pl["variant"], pl["quad_points"]))
     t_hbm = alg_bytes / (hbm * 1e9)
     bf16, bf16_kind = bf16_peak()
     t_f32 = flops / ((bf16 if tc else FP32_PEAK_TFLOPS) * 1e12)

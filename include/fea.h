@@ -79,9 +79,14 @@ typedef enum {
                         * compute-bound (the Neo-Hookean tangent at P2): both operands as
                         * hi + lo BF16 pairs, all four products on tcgen05 tensor cores with
                         * FP32 accumulation (<= 1e-5 relative); the per-point kinematics as
-                        * in FEA_PREC_FP32.  Every other (form, degree) runs the FP32
-                        * contraction in this mode (they are bound by HBM, not by the
-                        * contraction).  fea_assemble_batch accepts it; the fused batch does not. */
+                        * in FEA_PREC_FP32.  With FP32 output (out_f32 = 1) the
+                        * pre-evaluated mass and Helmholtz matrices at P1-P2 also run on the
+                        * tensor cores (one [128 elements x r] x [r x n^2] product per tile,
+                        * both operands split the same way), since without the FP64 stores
+                        * their contraction, not HBM, bounds them.  Every other (form,
+                        * degree, output) runs the FP32 contraction in this mode (bound by
+                        * HBM, not by the contraction).  fea_assemble_batch accepts it; the
+                        * fused batch does not. */
 } fea_precision;
 
 /* Loop-nest variant (Section 4, Figure "loopnest-opt"). */

@@ -187,8 +187,9 @@ int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, boo
 int make_plan(DevState* st, int form, int p, const fea_options& o, Plan* pl, bool batch, bool use_tuned) {
   static std::mutex mu;
   static std::map<std::vector<int64_t>, Plan> cache;
-  const std::vector<int64_t> key = {form, p, o.precision, o.variant, o.tile, (int64_t)o.smem_budget, batch ? 1 : 0,
-                                    st ? (int64_t)st->smem_optin : -1, use_tuned ? tuned_generation() : -1};
+  const std::vector<int64_t> key = {form, p, o.precision, o.out_f32, o.variant, o.tile, (int64_t)o.smem_budget,
+                                    batch ? 1 : 0, st ? (int64_t)st->smem_optin : -1,
+                                    use_tuned ? tuned_generation() : -1};
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -210,9 +211,12 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
   if (!valid_fd(form, p)) return fail(FEA_EINVAL, "unsupported form/degree");
   if (o.precision != FEA_PREC_FP64 && o.precision != FEA_PREC_FP32 && o.precision != FEA_PREC_BF16X2)
     return fail(FEA_EINVAL, "unsupported precision");
-  // split-BF16 tensor-core contraction where a kernel exists (the dense, compute-bound
-  // Neo-Hookean tangent); the other (form, degree) run the FP32 contraction
-  const KernelInfo* tc = o.precision == FEA_PREC_BF16X2 && !batch ? find_tc_kernel(form, p) : nullptr;
+  // split-BF16 tensor-core contraction where a kernel exists and the contraction is
+  // compute-bound: the Neo-Hookean tangent, and the pre-evaluated scalar forms with
+  // FP32 output (with FP64 output they are bound by HBM); the rest run the FP32 contraction
+  const bool scalar = form == FEA_MASS || form == FEA_HELMHOLTZ;
+  const KernelInfo* tc =
+      o.precision == FEA_PREC_BF16X2 && !batch && (!scalar || o.out_f32 == 1) ? find_tc_kernel(form, p) : nullptr;
   const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
   const size_t limit = st ? st->smem_optin : 232448;
   const size_t budget = o.smem_budget ? std::min(o.smem_budget, limit) : limit;
