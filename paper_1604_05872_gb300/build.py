@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfea.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["fea_api.cu", "batch.cu", "kernels_pre.cu", "kernels_se.cu", "kernels_naive.cu", "kernels_vec.cu", "kernels_tc.cu", "global.cu",
+SOURCES = ["fea_api.cu", "batch.cu", "kernels_pre.cu", "kernels_se.cu", "kernels_naive.cu", "kernels_vec.cu", "kernels_tc.cu", "kernels_pretc.cu", "global.cu",
            "bernstein.cu",
            "host_model.cpp", "planner.cpp", "opcount.cpp", "theta.cpp", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

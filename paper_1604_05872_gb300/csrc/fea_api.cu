@@ -21,6 +21,11 @@
 
 namespace fea {
 
+// The split-BF16 kernel of the pre-evaluated scalar forms (kernels_pretc.cu).
+const KernelInfo* find_pretc_kernel(int form, int p);
+bool is_pretc_kernel(const void* fn);
+bool pretc_table_words(int form, int p, std::vector<uint32_t>* words);
+
 bool tc_table_words(int form, int p, std::vector<uint32_t>* words);
 bool bernstein_table_words(int form, int p, std::vector<uint32_t>* words);
 const KernelInfo* find_tc_kernel(int form, int p);
@@ -104,7 +109,8 @@ int get_tables(DevState* st, int form, int p, int prec, TableEntry** out) {
   if (it == st->tables.end() && (prec == 2 || prec == 3)) {
     // 32-bit word tables: the tensor-core kernels (2) and the Bernstein variant (3)
     std::vector<uint32_t> words;
-    if (prec == 2 && !tc_table_words(form, p, &words)) return fail(FEA_EINVAL, "no tensor-core table for this form/degree");
+    if (prec == 2 && !tc_table_words(form, p, &words) && !pretc_table_words(form, p, &words))
+      return fail(FEA_EINVAL, "no tensor-core table for this form/degree");
     if (prec == 3 && !bernstein_table_words(form, p, &words)) return fail(FEA_EINVAL, "no Bernstein table for this form/degree");
     TableEntry te;
     te.lay.total = (int)words.size();
@@ -215,8 +221,9 @@ static int make_plan_uncached(DevState* st, int form, int p, const fea_options& 
   // compute-bound: the Neo-Hookean tangent, and the pre-evaluated scalar forms with
   // FP32 output (with FP64 output they are bound by HBM); the rest run the FP32 contraction
   const bool scalar = form == FEA_MASS || form == FEA_HELMHOLTZ;
-  const KernelInfo* tc =
-      o.precision == FEA_PREC_BF16X2 && !batch && (!scalar || o.out_f32 == 1) ? find_tc_kernel(form, p) : nullptr;
+  const KernelInfo* tc = nullptr;
+  if (o.precision == FEA_PREC_BF16X2 && !batch)
+    tc = scalar ? (o.out_f32 == 1 ? find_pretc_kernel(form, p) : nullptr) : find_tc_kernel(form, p);
   const int prec = o.precision == FEA_PREC_FP64 ? 0 : 1;
   const size_t limit = st ? st->smem_optin : 232448;
   const size_t budget = o.smem_budget ? std::min(o.smem_budget, limit) : limit;
@@ -320,8 +327,15 @@ int prepare_launch(DevState* st, const Plan& pl, int form, int p, int64_t E, con
       const int ceiling = (int)st->smem_optin - (int)fa.sharedSizeBytes;  // minus the kernel's static shared memory
       if ((int)smem_bytes > ceiling) return fail(FEA_EINVAL, "tile does not fit the device's shared memory");
       CUDA_TRY(cudaFuncSetAttribute(pl.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ceiling));
+      // the tensor-core kernels size their residency by shared memory (their tensor-memory
+      // columns must fit): ask for the largest shared-memory carveout, or the occupancy
+      // query counts one CTA per SM where two fit
+      if (pl.k->prec == 2)
+        CUDA_TRY(cudaFuncSetAttribute(pl.k->fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
       CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.k->fn, pl.k->threads ? pl.k->threads : NT,
                                                              smem_bytes));
+      if (is_pretc_kernel(pl.k->fn) && per_sm == 1) per_sm = 2;  // two fit by shared memory and tensor memory
       occ[key] = per_sm;
     } else {
       per_sm = it->second;

@@ -1,8 +1,6 @@
 // Tensor-core kernels of the split-operand precision (FEA_PREC_BF16X2) and the
 // device tables they read: the Neo-Hookean tangent at P2 (shared reference
-// operand, nh_tc.cuh) and at P3 (one product per element, nh_tce.cuh), and the
-// pre-evaluated mass and Helmholtz matrices at P1-P2 with FP32 output
-// (pre_tc.cuh).
+// operand, nh_tc.cuh) and at P3 (one product per element, nh_tce.cuh).
 #include <cstring>
 #include <vector>
 
@@ -10,7 +8,6 @@
 #include "launch.cuh"
 #include "nh_tc.cuh"
 #include "nh_tce.cuh"
-#include "pre_tc.cuh"
 
 namespace fea {
 
@@ -18,20 +15,13 @@ template <int P>
 size_t nh_tc_smem(int, int) { return NhTc<P>::SMEM; }
 template <int P>
 size_t nh_tce_smem(int, int) { return NhTcE<P>::SMEM; }
-template <int F, int P>
-size_t pre_tc_smem(int, int) { return PreTc<F, P>::SMEM; }
-#define PRETC(F, P)                                                                                            \
-  KernelInfo { reinterpret_cast<const void*>(&pre_tc_kernel<F, P>), V_PRE, F, P, 2, PreTc<F, P>::TE,          \
-               &pre_tc_smem<F, P>, PreTc<F, P>::TE, PreTc<F, P>::NTH, false }
 
 const KernelInfo kTcKernels[] = {
     KernelInfo{reinterpret_cast<const void*>(&nh_tc_kernel<2>), V_SE, NEOHOOKEAN, 2, 2, NhTc<2>::TE, &nh_tc_smem<2>,
                NhTc<2>::TE, NhTc<2>::NTH, true},
     KernelInfo{reinterpret_cast<const void*>(&nh_tce_kernel<3>), V_SE, NEOHOOKEAN, 3, 2, NhTcE<3>::TE, &nh_tce_smem<3>,
                NhTcE<3>::TE, NhTcE<3>::NTH, true},
-    PRETC(0, 1), PRETC(0, 2), PRETC(1, 1), PRETC(1, 2),
 };
-#undef PRETC
 const int kNumTcKernels = sizeof(kTcKernels) / sizeof(kTcKernels[0]);
 
 const KernelInfo* find_tc_kernel(int form, int p) {
@@ -126,35 +116,8 @@ static void nh_tce_table(std::vector<uint32_t>* words) {
     }
 }
 
-// The pre-evaluated reference tensors R_r[i][j] as the B operand of pre_tc_kernel:
-// row (i, j), K = r, three BF16 parts (the FP32 value rounded, then each remainder
-// rounded), part after part, in the K-major shared-memory layout the kernel
-// copies as it is.
-template <int F, int P>
-static void pre_tc_table(std::vector<uint32_t>* words) {
-  using C = PreTc<F, P>;
-  const Tables t = make_tables(F, P);
-  words->assign((size_t)3 * C::TABLE_WORDS, 0u);
-  const int ns = C::K::NS;
-  for (int r = 0; r < C::K::R; ++r)
-    for (int n = 0; n < C::K::NN; ++n) {
-      float rem = (float)t.R[(size_t)r * ns * ns + n];
-      const uint32_t off = C::kmajor_off(n, r);
-      const int sh = (off & 2u) ? 16 : 0;
-      for (int part = 0; part < 3; ++part) {
-        const uint16_t b = bf16_rn(rem);
-        (*words)[(size_t)part * C::TABLE_WORDS + (off >> 2)] |= (uint32_t)b << sh;
-        rem -= bf16_val(b);
-      }
-    }
-}
-
 // Device-table words of the tensor-core kernel of (form, p); false if there is none.
 bool tc_table_words(int form, int p, std::vector<uint32_t>* words) {
-  if (form == MASS && p == 1) return pre_tc_table<0, 1>(words), true;
-  if (form == MASS && p == 2) return pre_tc_table<0, 2>(words), true;
-  if (form == HELMHOLTZ && p == 1) return pre_tc_table<1, 1>(words), true;
-  if (form == HELMHOLTZ && p == 2) return pre_tc_table<1, 2>(words), true;
   if (form == NEOHOOKEAN && p == 2) {
     nh_tc_table<2>(words);
     return true;
