@@ -272,8 +272,8 @@ def precision_of(args, fea, form, p):
     names = {"fp32": fea.PREC_FP32, "bf16x2": fea.PREC_BF16X2, "fp64": fea.PREC_FP64}
     f32 = bool(args.out_f32)  # a tensor-core kernel exists where the split-BF16 plan differs from the FP32 one
     tc = fea.plan(form, p, precision=fea.PREC_BF16X2, out_f32=f32) != fea.plan(form, p, precision=fea.PREC_FP32, out_f32=f32)
-    if args.precision == "auto":  # the tensor cores where they are faster: the Neo-Hookean tangent
-        return (fea.PREC_BF16X2, "bf16x2", True) if tc and form == 3 else (fea.PREC_FP32, "fp32", False)
+    if args.precision == "auto":  # the tensor cores wherever the split-BF16 plan has a kernel for them
+        return (fea.PREC_BF16X2, "bf16x2", True) if tc else (fea.PREC_FP32, "fp32", False)
     prec = names[args.precision]
     return prec, args.precision, tc and prec == fea.PREC_BF16X2
 
