@@ -123,3 +123,30 @@ def test_bernstein_argument_checks_on_cpu(lib):
     assert lib.fea_assemble_bernstein(fea.HELMHOLTZ, 5, 10, nul, nul, nul, 0, nul) == fea.EINVAL
     assert lib.fea_assemble_bernstein(fea.HELMHOLTZ, 2, -1, nul, nul, nul, 0, nul) == fea.EINVAL
     assert lib.fea_assemble_bernstein(fea.HELMHOLTZ, 2, 10, nul, nul, nul, 2, nul) == fea.EINVAL
+
+
+def test_split_bf16_plan_selection_without_gpu(lib):
+    """The split-BF16 precision takes the tensor cores where the contraction is compute-bound: the
+    Neo-Hookean tangent (P2, P3) always, the pre-evaluated mass and Helmholtz matrices (P1, P2) only
+    with FP32 output; everything else keeps its FP32 plan."""
+    TC = fea.PREC_BF16X2
+    for form, p in [(fea.MASS, 1), (fea.MASS, 2), (fea.HELMHOLTZ, 1), (fea.HELMHOLTZ, 2)]:
+        tc = fea.plan(form, p, precision=TC, out_f32=True)
+        assert tc["tile"] == 128 and tc["threads"] == 256 and tc["variant"] == fea.VARIANT_PRE
+        assert tc != fea.plan(form, p, precision=fea.PREC_FP32, out_f32=True)
+        assert fea.plan(form, p, precision=TC) == fea.plan(form, p, precision=fea.PREC_FP32)
+        with pytest.raises(fea.FeaError):  # the tensor-core layout fixes its tile
+            fea.plan(form, p, precision=TC, out_f32=True, tile=96)
+    for form, p in [(fea.MASS, 3), (fea.HELMHOLTZ, 3), (fea.HELMHOLTZ, 4), (fea.ELASTICITY, 2)]:
+        assert fea.plan(form, p, precision=TC, out_f32=True) == fea.plan(form, p, precision=fea.PREC_FP32, out_f32=True)
+    for p in (2, 3):
+        assert fea.plan(fea.NEOHOOKEAN, p, precision=TC)["threads"] > 256
+
+
+def test_combined_global_assembly_argument_checks_without_gpu(lib):
+    """Host-side refusals of fea_assemble_csr_combined (no device memory touched)."""
+    for form, p in [(fea.ELASTICITY, 1), (fea.NEOHOOKEAN, 2), (fea.MASS, 4)]:
+        assert lib.fea_assemble_csr_combined(form, p, 10, None, None, None, 100, 10, None, None) == fea.EINVAL
+    # a plan shorter than its header for E elements
+    assert lib.fea_assemble_csr_combined(fea.MASS, 1, 1000, None, None, None, 5, 10, None, None) == fea.EINVAL
+    assert lib.fea_assemble_csr_combined(fea.MASS, 1, -1, None, None, None, 100, 10, None, None) == fea.EINVAL
